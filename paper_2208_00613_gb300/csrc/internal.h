@@ -1,0 +1,93 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace hbx {
+
+// ---- sampling (sample.cu) ----
+cudaError_t launch_sample_warp(const SampleArgs& a, uint32_t qw, int sms, cudaStream_t s);
+cudaError_t launch_sample_block(const SampleArgs& a, uint32_t nbig, uint32_t slots, cudaStream_t s);
+int block_path_threads();
+
+// ---- selection (select.cu) ----
+struct SelState {
+    uint32_t u;            // current u*
+    uint32_t it;           // iteration
+    uint32_t n_cov_huff, n_cov_bm, n_cov_raw, pad;
+    unsigned long long gain;     // sets covered by u* this iteration
+    unsigned long long covered;  // total covered
+};
+
+struct SelArgs {
+    uint32_t n, n4, T;
+    const SetRec* recs;
+    const uint32_t* raw_heap;
+    const uint32_t* code_heap;
+    const uint32_t* bm_heap;
+    DevCodebook cb;
+    uint32_t has_cb;
+    uint32_t hot;                          // ranks counted in shared memory
+    int32_t* cnt;                          // [n4]; -1 = chosen or padding
+    uint8_t* alive;                        // [T]
+    const unsigned long long* chunk_items; // (j << 32) | chunk
+    unsigned long long n_items;
+    const uint32_t* bm_sets;               // bitmap set ids
+    uint32_t n_bm;
+    SelState* st;
+    uint32_t* cov_huff;                    // sets covered this iteration, by kind
+    uint32_t* cov_bm;
+    uint32_t* cov_raw;
+    unsigned long long* partials;          // argmax per-block results
+    unsigned int* ticket;
+    uint32_t* seeds;                       // [k]
+    unsigned long long* marginal;          // [k]
+    int sms;
+};
+
+// Launch shapes used by the selection kernels (grids are fixed so that the k
+// iterations can be captured in one CUDA graph).
+struct SelShape {
+    uint32_t count_blocks, argmax_blocks, cover_blocks, dec_blocks;
+};
+SelShape sel_shape(int sms);
+
+cudaError_t launch_sel_init(const SelArgs& a, cudaStream_t s);
+cudaError_t launch_count(const SelArgs& a, uint32_t encode, cudaStream_t s);
+// one greedy iteration: argmax, cover test, decrements, finalize
+cudaError_t launch_iteration(const SelArgs& a, uint32_t encode, cudaStream_t s);
+cudaError_t launch_argmax(const SelArgs& a, cudaStream_t s);
+
+// ---- pool indexing and inspection (select.cu) ----
+struct IndexArgs {
+    const SetRec* recs;
+    uint32_t j0, j1;
+    unsigned long long* chunk_items;
+    unsigned long long items_cap;
+    uint32_t* bm_sets;
+    uint32_t bm_cap;
+    Counters* ctr;
+    double* moments;  // [4]: sum |R|, |R|^2, |R|^3, heap words held by the sets
+    uint32_t n;
+};
+cudaError_t launch_index(const IndexArgs& a, cudaStream_t s);
+
+struct DecodeArgs {
+    const SetRec* recs;
+    const uint32_t* raw_heap;
+    const uint32_t* code_heap;
+    const uint32_t* bm_heap;
+    DevCodebook cb;
+    uint32_t has_cb;
+    uint32_t n;
+    uint32_t j0, j1;
+    const unsigned long long* offsets;  // j1-j0+1, into out
+    uint32_t* out;
+    Counters* ctr;
+};
+cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);
+
+}  // namespace hbx

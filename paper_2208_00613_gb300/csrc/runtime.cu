@@ -1,0 +1,1193 @@
+// Host runtime of the library: contexts, graphs, RR pools, the IMM driver and
+// the C ABI (include/hbx.h).
+//
+// Compiled with -ffp-contract=off: the IMM bounds of Section 2.2 / Eq. (1) are
+// FP64 expressions whose rounding must not depend on contraction.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "hbx.h"
+#include "internal.h"
+#include "runtime.h"
+
+using namespace hbx;
+
+// ===========================================================================
+// errors and device memory
+// ===========================================================================
+namespace hbx {
+
+int fail(hbx_ctx* c, int code, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return code;
+}
+
+int cuda_fail(hbx_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, HBX_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int dalloc(hbx_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (c->alloc_fn) {
+        *p = c->alloc_fn(bytes, c->alloc_user);
+        if (!*p) return fail(c, HBX_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+        if (((uintptr_t)*p) & 255) {
+            c->free_fn(*p, c->alloc_user);
+            *p = nullptr;
+            return fail(c, HBX_ERR_INVALID_ARG, "allocator returned memory not 256-byte aligned");
+        }
+    } else {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return fail(c, HBX_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        }
+    }
+    c->live_bytes += bytes;
+    c->sizes[*p] = bytes;
+    return HBX_OK;
+}
+
+void dfree(hbx_ctx* c, void* p) {
+    if (!p) return;
+    auto it = c->sizes.find(p);
+    if (it != c->sizes.end()) {
+        c->live_bytes -= it->second;
+        c->sizes.erase(it);
+    }
+    if (c->free_fn) c->free_fn(p, c->alloc_user);
+    else cudaFree(p);
+}
+
+}  // namespace hbx
+
+#define CK(call)                                                 \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+#define RC(call)                  \
+    do {                          \
+        int r_ = (call);          \
+        if (r_ != HBX_OK) return r_; \
+    } while (0)
+
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ===========================================================================
+// context
+// ===========================================================================
+extern "C" const char* hbx_strerror(int code) {
+    switch (code) {
+        case HBX_OK: return "ok";
+        case HBX_ERR_INVALID_ARG: return "invalid argument";
+        case HBX_ERR_OOM: return "out of device memory";
+        case HBX_ERR_CUDA: return "CUDA error";
+        case HBX_ERR_TIMEOUT: return "timed out";
+        case HBX_ERR_WEIGHTS_GT_1: return "LT in-weights of a vertex sum above 1";
+        case HBX_ERR_ADMISSION: return "query can never fit the memory budget";
+        case HBX_ERR_CANCELLED: return "cancelled";
+        case HBX_ERR_INTERNAL: return "internal error";
+        default: return "unknown error";
+    }
+}
+
+extern "C" const char* hbx_last_error(const hbx_ctx* c) { return c ? c->last_error.c_str() : "no context"; }
+
+extern "C" void hbx_default_options(hbx_options* o) {
+    if (!o) return;
+    o->density_cut = 32;
+    o->warmup_sets = 0;
+    o->encode = 1;
+    o->form = 1;
+    o->pool_epoch = 0;
+    o->warp_capacity = 0;
+    o->max_device_bytes = 0;
+}
+
+extern "C" int hbx_create(hbx_ctx** out, int dev, void* stream) {
+    if (!out) return HBX_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || dev < 0 || dev >= ndev) {
+        cudaGetLastError();
+        return HBX_ERR_INVALID_ARG;
+    }
+    hbx_ctx* ctx = new hbx_ctx();
+    ctx->device = dev;
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return HBX_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+        ctx->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return HBX_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    *out = ctx;
+    return HBX_OK;
+}
+
+extern "C" int hbx_set_allocator(hbx_ctx* c, void* (*a)(size_t, void*), void (*f)(void*, void*), void* user) {
+    if (!c) return HBX_ERR_INVALID_ARG;
+    if ((a == nullptr) != (f == nullptr)) return fail(c, HBX_ERR_INVALID_ARG, "alloc and free must both be set");
+    if (!c->sizes.empty()) return fail(c, HBX_ERR_INVALID_ARG, "allocator must be set before any allocation");
+    c->alloc_fn = a;
+    c->free_fn = f;
+    c->alloc_user = user;
+    return HBX_OK;
+}
+
+void pool_free_all(hbx_pool* p);
+
+extern "C" void hbx_destroy(hbx_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    hbx_server_destroy_all(c);
+    for (hbx_pool* p : std::vector<hbx_pool*>(c->pools.begin(), c->pools.end())) hbx_pool_destroy(p);
+    for (hbx_graph* g : std::vector<hbx_graph*>(c->graphs.begin(), c->graphs.end())) hbx_graph_destroy(g);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// ===========================================================================
+// graphs
+// ===========================================================================
+extern "C" int hbx_graph_create(hbx_ctx* ctx, uint32_t n, uint64_t m, const uint32_t* row_ptr, const uint32_t* col,
+                                const float* ic_prob, const float* lt_weight, hbx_graph** out) {
+    if (!ctx || !out) return HBX_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 2 || n == 0xFFFFFFFFu) return fail(ctx, HBX_ERR_INVALID_ARG, "n must be in [2, 2^32-1)");
+    if (m >= (1ull << 32)) return fail(ctx, HBX_ERR_INVALID_ARG, "m must be below 2^32");
+    if (!row_ptr || (m && !col)) return fail(ctx, HBX_ERR_INVALID_ARG, "row_ptr/col missing");
+    if (!ic_prob && !lt_weight) return fail(ctx, HBX_ERR_INVALID_ARG, "no diffusion parameters");
+    if (row_ptr[0] != 0 || row_ptr[n] != m) return fail(ctx, HBX_ERR_INVALID_ARG, "row_ptr must run from 0 to m");
+    uint32_t max_deg = 0;
+    for (uint32_t v = 0; v < n; v++) {
+        if (row_ptr[v + 1] < row_ptr[v]) return fail(ctx, HBX_ERR_INVALID_ARG, "row_ptr decreases");
+        max_deg = std::max(max_deg, row_ptr[v + 1] - row_ptr[v]);
+    }
+    for (uint64_t e = 0; e < m; e++)
+        if (col[e] >= n) return fail(ctx, HBX_ERR_INVALID_ARG, "col id out of range");
+    if (ic_prob)
+        for (uint64_t e = 0; e < m; e++)
+            if (!(ic_prob[e] >= 0.0f && ic_prob[e] <= 1.0f))
+                return fail(ctx, HBX_ERR_INVALID_ARG, "IC probability outside [0,1]");
+    std::vector<uint32_t> q;
+    if (lt_weight) {
+        q.resize(m ? m : 1);
+        for (uint32_t v = 0; v < n; v++) {
+            uint64_t sum = 0;
+            for (uint64_t e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
+                const float w = lt_weight[e];
+                if (!(w >= 0.0f && w <= 1.0f)) return fail(ctx, HBX_ERR_INVALID_ARG, "LT weight outside [0,1]");
+                const uint64_t fx = (uint64_t)std::floor((double)w * 4294967296.0);
+                sum += fx;
+                q[e] = (uint32_t)std::min<uint64_t>(fx, 0xFFFFFFFFull);
+            }
+            if (sum > 4294967296ull)
+                return fail(ctx, HBX_ERR_WEIGHTS_GT_1, "LT in-weights of vertex " + std::to_string(v) + " sum above 1");
+        }
+    }
+    cudaSetDevice(ctx->device);
+    hbx_graph* g = new hbx_graph();
+    g->ctx = ctx;
+    g->n = n;
+    g->m = (uint32_t)m;
+    g->max_indeg = max_deg;
+    auto up = [&](void** dst, const void* src, size_t bytes, size_t alloc_bytes) -> int {
+        int r = dalloc(ctx, dst, alloc_bytes);
+        if (r) return r;
+        if (alloc_bytes > bytes) CK(cudaMemsetAsync((char*)*dst + bytes, 0, alloc_bytes - bytes, ctx->stream));
+        if (bytes) CK(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        return HBX_OK;
+    };
+    int r = up((void**)&g->row_ptr, row_ptr, ((size_t)n + 1) * 4, ((size_t)n + 1) * 4);
+    if (!r) r = up((void**)&g->col, col, m * 4, m * 4 + 16);
+    const size_t m4 = ((m + 3) / 4) * 4;
+    if (!r && ic_prob) r = up((void**)&g->prob, ic_prob, m * 4, m4 * 4 + 16);
+    if (!r && lt_weight) r = up((void**)&g->q, q.data(), m * 4, m * 4 + 16);
+    if (!r) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) r = cuda_fail(ctx, e, "graph upload");
+    }
+    if (r) {
+        dfree(ctx, g->row_ptr);
+        dfree(ctx, g->col);
+        dfree(ctx, g->prob);
+        dfree(ctx, g->q);
+        delete g;
+        return r;
+    }
+    ctx->graphs.insert(g);
+    *out = g;
+    return HBX_OK;
+}
+
+extern "C" void hbx_graph_destroy(hbx_graph* g) {
+    if (!g) return;
+    hbx_ctx* c = g->ctx;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (hbx_pool* p : std::vector<hbx_pool*>(c->pools.begin(), c->pools.end()))
+        if (p->g == g) hbx_pool_destroy(p);
+    dfree(c, g->row_ptr);
+    dfree(c, g->col);
+    dfree(c, g->prob);
+    dfree(c, g->q);
+    c->graphs.erase(g);
+    for (auto it = c->tuned.begin(); it != c->tuned.end();)
+        it = (it->first.first == g) ? c->tuned.erase(it) : std::next(it);
+    delete g;
+}
+
+// ===========================================================================
+// pools
+// ===========================================================================
+namespace hbx {
+
+static DevGraph dev_graph(const hbx_graph* g) {
+    DevGraph d;
+    d.n = g->n;
+    d.m = g->m;
+    d.row_ptr = g->row_ptr;
+    d.col = g->col;
+    d.prob = g->prob;
+    d.q = g->q;
+    return d;
+}
+
+static DevCodebook dev_codebook(const hbx_pool* p) {
+    DevCodebook c;
+    memset(&c, 0, sizeof(c));
+    if (!p->has_cb) return c;
+    c.rank_of = p->rank_of;
+    c.vertex_of_rank = p->vertex_of_rank;
+    c.len_of_rank = p->len_of_rank;
+    c.code_of_rank = p->code_of_rank;
+    c.lut = p->lut;
+    c.dec = p->dec;
+    c.nsym = p->nsym;
+    c.max_len = p->max_len;
+    return c;
+}
+
+static int pool_bytes_check(hbx_pool* p, size_t add) {
+    if (p->o.max_device_bytes && p->device_bytes + add > p->o.max_device_bytes)
+        return fail(p->ctx, HBX_ERR_OOM, "pool would exceed max_device_bytes");
+    return HBX_OK;
+}
+
+// (Re)allocate a zero-filled device array of `bytes`, keeping the first `keep` bytes.
+int grow_buffer(hbx_pool* p, void** buf, size_t old_bytes, size_t new_bytes, size_t keep) {
+    hbx_ctx* ctx = p->ctx;
+    RC(pool_bytes_check(p, new_bytes > old_bytes ? new_bytes - old_bytes : 0));
+    void* nb = nullptr;
+    RC(dalloc(ctx, &nb, new_bytes));
+    CK(cudaMemsetAsync(nb, 0, new_bytes, ctx->stream));
+    if (*buf && keep) CK(cudaMemcpyAsync(nb, *buf, keep, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (*buf) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        dfree(ctx, *buf);
+    }
+    *buf = nb;
+    p->device_bytes += new_bytes;
+    p->device_bytes -= old_bytes;
+    return HBX_OK;
+}
+
+static const uint64_t HEAP_SLACK = 64;  // words past the end, for the decoder's look-ahead
+
+static int grow_heap(hbx_pool* p, Heap& h, uint64_t need_words) {
+    if (need_words <= h.cap) return HBX_OK;
+    uint64_t nc = std::max<uint64_t>(need_words + need_words / 4, h.cap * 2);
+    nc = std::max<uint64_t>(nc, 1u << 16);
+    nc = (nc + 3) & ~3ull;
+    RC(grow_buffer(p, (void**)&h.d, h.d ? (h.cap + HEAP_SLACK) * 4 : 0, (nc + HEAP_SLACK) * 4, h.cap * 4));
+    h.cap = nc;
+    return HBX_OK;
+}
+
+static int ensure_recs(hbx_pool* p, uint64_t T) {
+    if (T <= p->rec_cap) return HBX_OK;
+    uint64_t nc = std::max<uint64_t>(T, p->rec_cap * 2);
+    nc = std::max<uint64_t>(nc, 4096);
+    void* b = p->recs;
+    // new records are KIND_PENDING (0xFF bytes in kind) until written
+    hbx_ctx* ctx = p->ctx;
+    RC(pool_bytes_check(p, (nc - p->rec_cap) * sizeof(SetRec)));
+    void* nb = nullptr;
+    RC(dalloc(ctx, &nb, nc * sizeof(SetRec)));
+    CK(cudaMemsetAsync(nb, 0xFF, nc * sizeof(SetRec), ctx->stream));
+    if (b) {
+        CK(cudaMemcpyAsync(nb, b, p->rec_cap * sizeof(SetRec), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        dfree(ctx, b);
+    }
+    p->device_bytes += (nc - p->rec_cap) * sizeof(SetRec);
+    p->recs = (SetRec*)nb;
+    p->rec_cap = nc;
+    return HBX_OK;
+}
+
+static int ensure_lists(hbx_pool* p, uint64_t count) {
+    if (count <= p->list_cap) return HBX_OK;
+    uint64_t nc = std::max<uint64_t>(count, p->list_cap * 2);
+    RC(grow_buffer(p, (void**)&p->big_list, p->list_cap * 4, nc * 4, 0));
+    RC(grow_buffer(p, (void**)&p->retry_list, p->list_cap * 4, nc * 4, 0));
+    RC(grow_buffer(p, (void**)&p->list_in, p->list_cap * 4, nc * 4, 0));
+    p->list_cap = nc;
+    return HBX_OK;
+}
+
+static int ensure_block_scratch(hbx_pool* p, uint32_t slots) {
+    if (slots <= p->bp_slots) return HBX_OK;
+    const uint64_t words = p->bp_words;
+    const uint64_t n = p->g->n;
+    RC(grow_buffer(p, (void**)&p->bp_visited, p->bp_slots * words * 4, slots * words * 4, 0));
+    RC(grow_buffer(p, (void**)&p->bp_rbits, p->bp_slots * words * 4, slots * words * 4, 0));
+    RC(grow_buffer(p, (void**)&p->bp_aux, p->bp_slots * words * 4, slots * words * 4, 0));
+    RC(grow_buffer(p, (void**)&p->bp_queue, p->bp_slots * n * 4, slots * n * 4, 0));
+    p->bp_slots = slots;
+    return HBX_OK;
+}
+
+static int read_counters(hbx_pool* p) {
+    hbx_ctx* ctx = p->ctx;
+    CK(cudaMemcpyAsync(&p->hc, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (p->hc.error) return fail(ctx, HBX_ERR_INTERNAL, "kernel error code " + std::to_string(p->hc.error));
+    return HBX_OK;
+}
+
+// zero the per-launch fields of the device counters
+static int reset_launch_counters(hbx_pool* p) {
+    hbx_ctx* ctx = p->ctx;
+    CK(cudaMemsetAsync(p->ctr, 0, 2 * sizeof(unsigned long long), ctx->stream));  // work, big_work
+    CK(cudaMemsetAsync(&p->ctr->big_count, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    return HBX_OK;
+}
+
+static SampleArgs sample_args(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, const uint32_t* list,
+                              uint32_t* freq, uint32_t cut) {
+    SampleArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = dev_graph(p->g);
+    a.key0 = (uint32_t)p->seed;
+    a.key1 = (uint32_t)(p->seed >> 32);
+    a.epoch = p->o.pool_epoch;
+    a.model = (uint32_t)p->model;
+    a.mode = mode;
+    a.cut = cut;
+    a.j0 = j0;
+    a.count = count;
+    a.list = list;
+    a.persistent = p->o.form ? 1u : 0u;
+    a.freq = freq;
+    a.recs = p->recs;
+    a.raw_heap = p->raw.d;
+    a.raw_cap = p->raw.cap;
+    a.code_heap = p->code.d;
+    a.code_cap = p->code.cap;
+    a.bm_heap = p->bm.d;
+    a.bm_cap = p->bm.cap;
+    a.cb = dev_codebook(p);
+    a.big_list = p->big_list;
+    a.retry_list = p->retry_list;
+    a.ctr = p->ctr;
+    a.bp_visited = p->bp_visited;
+    a.bp_rbits = p->bp_rbits;
+    a.bp_queue = p->bp_queue;
+    a.bp_aux = p->bp_aux;
+    a.bp_words = p->bp_words;
+    return a;
+}
+
+// Sample sets (range [j0, j0+count) or list) in `mode`, handling sets too large
+// for a warp and heaps that run out.  The list, if any, is a device array.
+static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, const uint32_t* list,
+                      uint32_t* freq, uint32_t cut, uint32_t qw) {
+    hbx_ctx* ctx = p->ctx;
+    for (int attempt = 0; count > 0; attempt++) {
+        if (attempt > 40) return fail(ctx, HBX_ERR_INTERNAL, "sampling retries did not converge");
+        RC(ensure_lists(p, count));
+        RC(reset_launch_counters(p));
+        const bool timed = mode != MODE_HIST;
+        SampleArgs a = sample_args(p, mode, j0, count, list, freq, cut);
+        if (timed) CK(cudaEventRecord(p->ev0, ctx->stream));
+        CK(launch_sample_warp(a, qw, ctx->sms, ctx->stream));
+        if (timed) CK(cudaEventRecord(p->ev1, ctx->stream));
+        p->launches++;
+        RC(read_counters(p));
+        if (timed) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+            p->sample_kernel_s += ms * 1e-3;
+            p->sample_kernel_launches++;
+        }
+        const uint32_t nbig = (uint32_t)p->hc.big_count;
+        if (nbig) {
+            const uint32_t slots = std::min<uint32_t>(nbig, (uint32_t)ctx->sms * 2);
+            RC(ensure_block_scratch(p, slots));
+            a = sample_args(p, mode, j0, count, list, freq, cut);
+            if (timed) CK(cudaEventRecord(p->ev0, ctx->stream));
+            CK(launch_sample_block(a, nbig, slots, ctx->stream));
+            if (timed) CK(cudaEventRecord(p->ev1, ctx->stream));
+            p->launches++;
+            RC(read_counters(p));
+            if (timed) {
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+                p->sample_kernel_s += ms * 1e-3;
+                p->sample_kernel_launches++;
+            }
+        }
+        const uint32_t nretry = (uint32_t)p->hc.retry_count;
+        if (nretry == 0) break;
+        // grow whichever heap overflowed, then redo the listed sets
+        RC(grow_heap(p, p->raw, p->hc.raw_cursor + 1024));
+        RC(grow_heap(p, p->code, p->hc.code_cursor + 1024));
+        const uint64_t row = (((uint64_t)p->g->n + 31) / 32 + 3) & ~3ull;
+        RC(grow_heap(p, p->bm, p->hc.bm_cursor + (p->hc.bm_cursor > p->bm.cap ? 8 * row : 0)));
+        CK(cudaMemcpyAsync(p->list_in, p->retry_list, (size_t)nretry * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        list = p->list_in;
+        count = nretry;
+        j0 = 0;
+    }
+    return HBX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Codebook (Section 4.2.2): Huffman code lengths from the warm-up frequencies,
+// then canonical codes.  Rules (the paper names BuildHuffmanCode only):
+// symbols = vertices with f > 0 taken in (f, id) order; each merge takes the
+// two lightest queue fronts, preferring a leaf over an internal node of equal
+// weight; a lone symbol gets length 1; lengths over 32 trigger f = ceil(f/2)
+// (at least 1) and a rebuild.  Canonical codes: ranks in (length, id) order,
+// code(first of length L) = (code(first of L-1) + count(L-1)) << 1.
+// ---------------------------------------------------------------------------
+static void huffman_code_lengths(const std::vector<uint32_t>& sym, std::vector<uint64_t> w,
+                                 std::vector<uint8_t>& len_out) {
+    const size_t S = sym.size();
+    len_out.assign(S, 0);
+    if (S == 0) return;
+    if (S == 1) {
+        len_out[0] = 1;
+        return;
+    }
+    for (;;) {
+        // order leaves by (weight, id): ids are increasing in `sym`, so a stable
+        // bucket pass on weight keeps id order among equal weights
+        std::vector<uint32_t> leaf(S);
+        {
+            std::vector<std::pair<uint64_t, uint32_t>> kv(S);
+            for (size_t i = 0; i < S; i++) kv[i] = {w[i], (uint32_t)i};
+            std::stable_sort(kv.begin(), kv.end(),
+                             [](const std::pair<uint64_t, uint32_t>& x, const std::pair<uint64_t, uint32_t>& y) {
+                                 return x.first < y.first;
+                             });
+            for (size_t i = 0; i < S; i++) leaf[i] = kv[i].second;
+        }
+        // node ids: leaves 0..S-1, internal S..2S-2
+        std::vector<uint64_t> nw(2 * S - 1);
+        std::vector<uint32_t> up(2 * S - 1, 0);
+        for (size_t i = 0; i < S; i++) nw[i] = w[i];
+        size_t li = 0, qi = S, qe = S;
+        auto pick = [&]() -> uint32_t {
+            if (li < S && (qi == qe || nw[leaf[li]] <= nw[qi])) return leaf[li++];
+            return (uint32_t)qi++;
+        };
+        while (qe < 2 * S - 1) {
+            const uint32_t x = pick(), y = pick();
+            nw[qe] = nw[x] + nw[y];
+            up[x] = up[y] = (uint32_t)qe;
+            qe++;
+        }
+        std::vector<uint32_t> depth(2 * S - 1, 0);
+        uint32_t maxd = 0;
+        for (size_t v = 2 * S - 1; v-- > 0;) {
+            if (v == 2 * S - 2) continue;
+            depth[v] = depth[up[v]] + 1;
+            if (v < S) maxd = std::max(maxd, depth[v]);
+        }
+        if (maxd <= 32) {
+            for (size_t i = 0; i < S; i++) len_out[i] = (uint8_t)depth[i];
+            return;
+        }
+        for (auto& x : w) x = std::max<uint64_t>(1, (x + 1) / 2);
+    }
+}
+
+static int build_codebook(hbx_pool* p, const std::vector<uint32_t>& freq) {
+    hbx_ctx* ctx = p->ctx;
+    const uint32_t n = p->g->n;
+    std::vector<uint32_t> sym;
+    std::vector<uint64_t> w;
+    for (uint32_t v = 0; v < n; v++)
+        if (freq[v]) {
+            sym.push_back(v);
+            w.push_back(freq[v]);
+        }
+    std::vector<uint8_t> L;
+    huffman_code_lengths(sym, w, L);
+    uint32_t bl_count[34] = {0};
+    for (uint8_t x : L) bl_count[x]++;
+    bl_count[0] = 0;
+    // first code and first rank of each length (RFC 1951 Section 3.2.2 recurrence)
+    uint32_t first_code[33] = {0}, first_rank[33] = {0};
+    for (int b = 2; b <= 32; b++) {
+        first_code[b] = (first_code[b - 1] + bl_count[b - 1]) << 1;
+        first_rank[b] = first_rank[b - 1] + bl_count[b - 1];
+    }
+    const uint32_t S = (uint32_t)sym.size();
+    std::vector<uint32_t> rank_of(n, NONE), vor(std::max<uint32_t>(S, 1)), cor(std::max<uint32_t>(S, 1));
+    std::vector<uint8_t> lor(std::max<uint32_t>(S, 1));
+    std::vector<uint32_t> next_rank(first_rank, first_rank + 33);
+    p->h_len.assign(n, 0);
+    p->h_code.assign(n, 0);
+    uint32_t maxL = 0;
+    for (uint32_t i = 0; i < S; i++) {  // ids ascending
+        const uint32_t l = L[i];
+        const uint32_t r = next_rank[l]++;
+        const uint32_t c = first_code[l] + (r - first_rank[l]);
+        rank_of[sym[i]] = r;
+        vor[r] = sym[i];
+        cor[r] = c;
+        lor[r] = (uint8_t)l;
+        p->h_len[sym[i]] = l;
+        p->h_code[sym[i]] = c;
+        maxL = std::max(maxL, l);
+    }
+    std::vector<uint32_t> lut(1u << LUT_BITS, 0);
+    for (uint32_t r = 0; r < S; r++) {
+        const uint32_t l = lor[r];
+        if (l > (uint32_t)LUT_BITS) continue;
+        const uint32_t lo = cor[r] << (LUT_BITS - l), hi = (cor[r] + 1) << (LUT_BITS - l);
+        for (uint32_t x = lo; x < hi; x++) lut[x] = (r << 6) | l;
+    }
+    std::vector<uint32_t> dec(99, 0);
+    for (int b = 0; b <= 32; b++) {
+        dec[b] = first_code[b];
+        dec[33 + b] = b ? bl_count[b] : 0;
+        dec[66 + b] = first_rank[b];
+    }
+    p->h_rank = rank_of;
+    p->h_freq = freq;
+    p->nsym = S;
+    p->max_len = maxL;
+    auto up = [&](void** dst, const void* src, size_t bytes) -> int {
+        RC(grow_buffer(p, dst, 0, bytes + 16, 0));
+        CK(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        return HBX_OK;
+    };
+    RC(up((void**)&p->rank_of, rank_of.data(), (size_t)n * 4));
+    RC(up((void**)&p->vertex_of_rank, vor.data(), vor.size() * 4));
+    RC(up((void**)&p->code_of_rank, cor.data(), cor.size() * 4));
+    RC(up((void**)&p->len_of_rank, lor.data(), lor.size()));
+    RC(up((void**)&p->lut, lut.data(), lut.size() * 4));
+    RC(up((void**)&p->dec, dec.data(), dec.size() * 4));
+    CK(cudaStreamSynchronize(ctx->stream));
+    p->has_cb = true;
+    return HBX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: pick the warp capacity QW (the set size above which a set moves
+// from a warp to a whole block) by timing a calibration batch, per graph and
+// model; cached in the context.
+// ---------------------------------------------------------------------------
+static int choose_qw(hbx_pool* p, uint32_t* qw_out) {
+    hbx_ctx* ctx = p->ctx;
+    if (p->o.warp_capacity) {
+        *qw_out = p->o.warp_capacity;
+        return HBX_OK;
+    }
+    auto key = std::make_pair((const hbx_graph*)p->g, (int)p->model);
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        *qw_out = it->second;
+        return HBX_OK;
+    }
+    const uint32_t cands[4] = {128, 256, 512, 1024};
+    const uint32_t ncal = 8192;
+    uint32_t* freq = nullptr;
+    RC(grow_buffer(p, (void**)&freq, 0, (size_t)p->g->n * 4, 0));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    uint32_t best = 256;
+    const uint32_t base = 0x40000000u;  // calibration ids, never part of a pool prefix
+    const unsigned long long sc0 = p->hc.edges_scanned, lv0 = p->hc.edges_live;
+    for (int rep = 0; rep < 2; rep++) {
+        for (uint32_t qw : cands) {
+            CK(cudaEventRecord(e0, ctx->stream));
+            int r = run_sample(p, MODE_HIST, base, ncal, nullptr, freq, 0u, qw);
+            if (r) {
+                dfree(ctx, freq);
+                return r;
+            }
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep == 1 && ms < best_ms) {
+                best_ms = ms;
+                best = qw;
+            }
+        }
+    }
+    p->aux_scanned += p->hc.edges_scanned - sc0;
+    p->aux_live += p->hc.edges_live - lv0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(ctx, freq);
+    p->device_bytes -= (size_t)p->g->n * 4;
+    ctx->tuned[key] = best;
+    *qw_out = best;
+    return HBX_OK;
+}
+
+int pool_set_warmup(hbx_pool* p, uint64_t W) {
+    if (p->has_cb) return HBX_OK;
+    p->W = W;
+    return HBX_OK;
+}
+
+static int ensure_codebook(hbx_pool* p) {
+    hbx_ctx* ctx = p->ctx;
+    if (!p->o.encode || p->has_cb) return HBX_OK;
+    if (p->W == 0) return fail(ctx, HBX_ERR_INVALID_ARG, "encoded pool needs warmup_sets > 0");
+    if (p->W >= (1ull << 32)) return fail(ctx, HBX_ERR_INVALID_ARG, "warm-up block too large");
+    uint32_t* freq = nullptr;
+    const uint32_t n = p->g->n;
+    RC(grow_buffer(p, (void**)&freq, 0, (size_t)n * 4, 0));
+    const unsigned long long sc0 = p->hc.edges_scanned, lv0 = p->hc.edges_live;
+    int r = run_sample(p, MODE_HIST, 0, (uint32_t)p->W, nullptr, freq, p->o.density_cut, p->qw);
+    p->aux_scanned += p->hc.edges_scanned - sc0;
+    p->aux_live += p->hc.edges_live - lv0;
+    std::vector<uint32_t> hf(n);
+    if (!r) {
+        cudaError_t e = cudaMemcpyAsync(hf.data(), freq, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) r = cuda_fail(ctx, e, "warm-up histogram");
+    }
+    dfree(ctx, freq);
+    p->device_bytes -= (size_t)n * 4;
+    if (r) return r;
+    return build_codebook(p, hf);
+}
+
+int pool_extend(hbx_pool* p, uint64_t T) {
+    hbx_ctx* ctx = p->ctx;
+    if (T <= p->T) return HBX_OK;
+    if (T >= (1ull << 32)) return fail(ctx, HBX_ERR_INVALID_ARG, "pools hold fewer than 2^32 sets");
+    cudaSetDevice(ctx->device);
+    const double t0 = now_s();
+    if (!p->qw) RC(choose_qw(p, &p->qw));
+    RC(ensure_codebook(p));
+    RC(ensure_recs(p, T));
+    const uint32_t mode = p->o.encode ? MODE_ENCODE : MODE_RAW;
+    const uint64_t batch_max = 1ull << 22;
+    while (p->T < T) {
+        const uint64_t j0 = p->T;
+        const uint32_t count = (uint32_t)std::min<uint64_t>(T - j0, batch_max);
+        const unsigned long long verts_before = p->hc.rr_vertices;
+        RC(run_sample(p, mode, (uint32_t)j0, count, nullptr, nullptr, p->o.density_cut, p->qw));
+        // selection index of the new sets
+        const uint64_t added = p->hc.rr_vertices - verts_before;
+        const uint64_t items_need = p->hc.chunk_items + added / 32 + 2ull * count + 16;
+        if (items_need > p->items_cap) {
+            const uint64_t nc = std::max<uint64_t>(items_need + items_need / 4, p->items_cap * 2);
+            RC(grow_buffer(p, (void**)&p->items, p->items_cap * 8, nc * 8, p->hc.chunk_items * 8));
+            p->items_cap = nc;
+        }
+        const uint64_t bm_need = p->hc.bm_list + count;
+        if (bm_need > p->bm_list_cap) {
+            const uint64_t nc = std::max<uint64_t>(bm_need + bm_need / 4, p->bm_list_cap * 2);
+            RC(grow_buffer(p, (void**)&p->bm_sets, p->bm_list_cap * 4, nc * 4, p->hc.bm_list * 4));
+            p->bm_list_cap = nc;
+        }
+        IndexArgs ia;
+        ia.recs = p->recs;
+        ia.j0 = (uint32_t)j0;
+        ia.j1 = (uint32_t)(j0 + count);
+        ia.chunk_items = p->items;
+        ia.items_cap = p->items_cap;
+        ia.bm_sets = p->bm_sets;
+        ia.bm_cap = (uint32_t)std::min<uint64_t>(p->bm_list_cap, 0xFFFFFFFFull);
+        ia.ctr = p->ctr;
+        ia.moments = p->moments;
+        ia.n = p->g->n;
+        CK(launch_index(ia, ctx->stream));
+        p->launches++;
+        RC(read_counters(p));
+        p->T = j0 + count;
+    }
+    p->sample_s += now_s() - t0;
+    return HBX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// selection
+// ---------------------------------------------------------------------------
+static int ensure_sel(hbx_pool* p, uint64_t T, uint32_t k) {
+    const uint32_t n4 = (p->g->n + 3) & ~3u;
+    if (!p->cnt) {
+        RC(grow_buffer(p, (void**)&p->cnt, 0, (size_t)n4 * 4, 0));
+        RC(grow_buffer(p, (void**)&p->st, 0, sizeof(SelState), 0));
+        RC(grow_buffer(p, (void**)&p->partials, 0, (size_t)p->ctx->sms * 8 * 8, 0));
+        RC(grow_buffer(p, (void**)&p->ticket, 0, 256, 0));
+    }
+    if (T > p->alive_cap) {
+        const uint64_t nc = std::max<uint64_t>(T, p->alive_cap * 2);
+        RC(grow_buffer(p, (void**)&p->alive, p->alive_cap, nc, 0));
+        RC(grow_buffer(p, (void**)&p->cov_huff, p->alive_cap * 4, nc * 4, 0));
+        RC(grow_buffer(p, (void**)&p->cov_bm, p->alive_cap * 4, nc * 4, 0));
+        RC(grow_buffer(p, (void**)&p->cov_raw, p->alive_cap * 4, nc * 4, 0));
+        p->alive_cap = nc;
+    }
+    if (k > p->kcap) {
+        RC(grow_buffer(p, (void**)&p->d_seeds, p->kcap * 4, (size_t)k * 4, 0));
+        RC(grow_buffer(p, (void**)&p->d_marg, p->kcap * 8, (size_t)k * 8, 0));
+        p->kcap = k;
+    }
+    return HBX_OK;
+}
+
+static SelArgs sel_args(hbx_pool* p, uint64_t T) {
+    SelArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = p->g->n;
+    a.n4 = (p->g->n + 3) & ~3u;
+    a.T = (uint32_t)T;
+    a.recs = p->recs;
+    a.raw_heap = p->raw.d;
+    a.code_heap = p->code.d;
+    a.bm_heap = p->bm.d;
+    a.cb = dev_codebook(p);
+    a.has_cb = p->has_cb ? 1u : 0u;
+    a.hot = p->has_cb ? std::min<uint32_t>(p->nsym, 12288u) : 0u;
+    a.cnt = p->cnt;
+    a.alive = p->alive;
+    a.chunk_items = p->items;
+    a.n_items = p->hc.chunk_items;
+    a.bm_sets = p->bm_sets;
+    a.n_bm = (uint32_t)p->hc.bm_list;
+    a.st = (SelState*)p->st;
+    a.cov_huff = p->cov_huff;
+    a.cov_bm = p->cov_bm;
+    a.cov_raw = p->cov_raw;
+    a.partials = p->partials;
+    a.ticket = p->ticket;
+    a.seeds = p->d_seeds;
+    a.marginal = p->d_marg;
+    a.sms = p->ctx->sms;
+    return a;
+}
+
+int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* marginal, uint64_t* covered) {
+    hbx_ctx* ctx = p->ctx;
+    if (T == 0 || T > p->T) return fail(ctx, HBX_ERR_INVALID_ARG, "T must be in [1, pool size]");
+    if (k == 0 || k > p->g->n) return fail(ctx, HBX_ERR_INVALID_ARG, "k must be in [1, n]");
+    cudaSetDevice(ctx->device);
+    const double t0 = now_s();
+    RC(ensure_sel(p, T, k));
+    const SelArgs a = sel_args(p, T);
+    const uint32_t enc = p->o.encode;
+    CK(launch_sel_init(a, ctx->stream));
+    CK(launch_count(a, enc, ctx->stream));
+    const uint64_t per_it = 3 + (enc ? (uint64_t)(a.has_cb ? 1 : 0) + (a.n_bm ? 1 : 0) : 1);
+    p->launches += 1 + (enc ? (uint64_t)((a.n_items && a.has_cb) ? 1 : 0) + (a.n_bm ? 1 : 0) : 1) + per_it * k;
+    if (p->o.form) {
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaSuccess;
+        for (uint32_t it = 0; it < k && le == cudaSuccess; it++) le = launch_iteration(a, enc, ctx->stream);
+        cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+        if (le != cudaSuccess) return cuda_fail(ctx, le, "selection capture");
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        if (ie != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+        }
+        cudaError_t le2 = cudaGraphLaunch(exec, ctx->stream);
+        cudaError_t se = cudaStreamSynchronize(ctx->stream);
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (le2 != cudaSuccess) return cuda_fail(ctx, le2, "cudaGraphLaunch");
+        if (se != cudaSuccess) return cuda_fail(ctx, se, "selection");
+    } else {
+        SelState hs;
+        for (uint32_t it = 0; it < k; it++) {
+            CK(launch_iteration(a, enc, ctx->stream));
+            CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+    }
+    SelState hs;
+    std::vector<unsigned long long> hm(k);
+    CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(seeds, p->d_seeds, (size_t)k * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hm.data(), p->d_marg, (size_t)k * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (hs.pad) return fail(ctx, HBX_ERR_INTERNAL, "undecodable Huffman stream during selection");
+    if (hs.it != k) return fail(ctx, HBX_ERR_INTERNAL, "selection ran " + std::to_string(hs.it) + " iterations");
+    if (marginal)
+        for (uint32_t i = 0; i < k; i++) marginal[i] = hm[i];
+    if (covered) *covered = hs.covered;
+    p->select_s += now_s() - t0;
+    return HBX_OK;
+}
+
+}  // namespace hbx
+
+extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint64_t seed, const hbx_options* opts,
+                               hbx_pool** out) {
+    if (!ctx || !g || !out) return HBX_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (model != HBX_IC && model != HBX_LT) return fail(ctx, HBX_ERR_INVALID_ARG, "unknown model");
+    if (model == HBX_IC && !g->prob) return fail(ctx, HBX_ERR_INVALID_ARG, "graph has no IC probabilities");
+    if (model == HBX_LT && !g->q) return fail(ctx, HBX_ERR_INVALID_ARG, "graph has no LT weights");
+    hbx_options o;
+    hbx_default_options(&o);
+    if (opts) o = *opts;
+    if (o.density_cut == 0) o.density_cut = 32;
+    if (o.encode > 1 || o.form > 1) return fail(ctx, HBX_ERR_INVALID_ARG, "encode and form are 0 or 1");
+    if (o.warp_capacity && (o.warp_capacity < 64 || o.warp_capacity > 2048 ||
+                            (o.warp_capacity & (o.warp_capacity - 1))))
+        return fail(ctx, HBX_ERR_INVALID_ARG, "warp_capacity must be a power of two in [64, 2048]");
+    cudaSetDevice(ctx->device);
+    hbx_pool* p = new hbx_pool();
+    p->ctx = ctx;
+    p->g = g;
+    p->model = model;
+    p->seed = seed;
+    p->o = o;
+    p->W = o.warmup_sets;
+    p->bp_words = (((uint64_t)g->n + 31) / 32 + 3) & ~3ull;
+    int r = grow_buffer(p, (void**)&p->ctr, 0, sizeof(Counters), 0);
+    if (!r) r = grow_buffer(p, (void**)&p->moments, 0, 4 * sizeof(double), 0);
+    if (!r && (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess))
+        r = fail(ctx, HBX_ERR_CUDA, "cudaEventCreate");
+    if (!r) {
+        memset(&p->hc, 0, sizeof(p->hc));
+        ctx->pools.insert(p);
+        *out = p;
+        return HBX_OK;
+    }
+    dfree(ctx, p->ctr);
+    dfree(ctx, p->moments);
+    delete p;
+    return r;
+}
+
+extern "C" void hbx_pool_destroy(hbx_pool* p) {
+    if (!p) return;
+    hbx_ctx* c = p->ctx;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    void* bufs[] = {p->recs, p->raw.d, p->code.d, p->bm.d, p->ctr, p->moments, p->rank_of, p->vertex_of_rank,
+                    p->code_of_rank, p->len_of_rank, p->lut, p->dec, p->items, p->bm_sets, p->big_list,
+                    p->retry_list, p->list_in, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
+                    p->alive, p->cov_huff, p->cov_bm, p->cov_raw, p->st, p->partials, p->ticket, p->d_seeds,
+                    p->d_marg};
+    for (void* b : bufs) dfree(c, b);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    c->pools.erase(p);
+    delete p;
+}
+
+extern "C" int hbx_pool_extend(hbx_pool* p, uint64_t T) {
+    if (!p) return HBX_ERR_INVALID_ARG;
+    return pool_extend(p, T);
+}
+
+extern "C" uint64_t hbx_pool_size(const hbx_pool* p) { return p ? p->T : 0; }
+
+extern "C" int hbx_pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* marginal,
+                               uint64_t* covered) {
+    if (!p || !seeds) return HBX_ERR_INVALID_ARG;
+    return pool_select(p, T, k, seeds, marginal, covered);
+}
+
+// ===========================================================================
+// IMM (Section 2.2, Eq. (1)), read as IMM's own bounds with eps' = sqrt(2) eps:
+//   l'      = l (1 + ln 2 / ln n)
+//   lambda' = (2 + 2 eps'/3)(ln C(n,k) + l' ln n + ln log2 n) n / eps'^2
+//   lambda* = 2 n ((1 - 1/e) alpha + beta)^2 / eps^2,
+//   alpha = sqrt(l' ln n + ln 2), beta = sqrt((1 - 1/e)(ln C(n,k) + l' ln n + ln 2))
+// Round i = 1 .. floor(log2 n) - 1: x = n / 2^i, T_i = max(T_{i-1}, ceil(lambda'/x)),
+// greedy on [0, T_i); stop when n cov / T_i >= (1 + eps') x with
+// LB = (n cov / T_i) / (1 + eps').  Final theta = max(T_i, ceil(lambda*/LB)).
+// ===========================================================================
+namespace hbx {
+
+struct ImmBounds {
+    double epsp, ellp, lnc, lambda_p, lambda_star;
+};
+
+static bool imm_bounds(uint32_t n, uint32_t k, double eps, double ell, ImmBounds* b) {
+    if (n < 2 || k == 0 || k > n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0)) return false;
+    const double dn = (double)n;
+    const double epsp = std::sqrt(2.0) * eps;
+    const double ellp = ell * (1.0 + std::log(2.0) / std::log(dn));
+    double lnc = 0.0;
+    for (uint32_t i = 1; i <= k; i++) lnc += std::log(((double)(n - k) + (double)i) / (double)i);
+    const double lambda_p =
+        (2.0 + 2.0 * epsp / 3.0) * (lnc + ellp * std::log(dn) + std::log(std::log2(dn))) * dn / (epsp * epsp);
+    const double e1 = 1.0 - std::exp(-1.0);
+    const double alpha = std::sqrt(ellp * std::log(dn) + std::log(2.0));
+    const double beta = std::sqrt(e1 * (lnc + ellp * std::log(dn) + std::log(2.0)));
+    const double s = e1 * alpha + beta;
+    b->epsp = epsp;
+    b->ellp = ellp;
+    b->lnc = lnc;
+    b->lambda_p = lambda_p;
+    b->lambda_star = 2.0 * dn * s * s / (eps * eps);
+    return true;
+}
+
+static uint32_t ilog2_floor(uint32_t n) { return 31u - (uint32_t)__builtin_clz(n); }
+
+void fill_stats(hbx_pool* p, hbx_stats* s) {
+    memset(s, 0, sizeof(*s));
+    s->theta = p->T;
+    s->sets_huffman = p->hc.sets_huff;
+    s->sets_bitmap = p->hc.sets_bm;
+    s->sets_raw = p->hc.sets_raw;
+    s->sets_big = p->hc.sets_big;
+    s->rr_vertices = p->hc.rr_vertices;
+    s->edges_scanned = p->hc.edges_scanned - p->aux_scanned;
+    s->edges_live = p->hc.edges_live - p->aux_live;
+    s->code_bits = p->hc.code_bits;
+    s->warmup_sets = p->o.encode ? p->W : 0;
+    s->warp_capacity = p->qw;
+    double mom[4] = {0, 0, 0, 0};
+    cudaMemcpyAsync(mom, p->moments, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->ctx->stream);
+    cudaStreamSynchronize(p->ctx->stream);
+    // bytes actually held by the sets (heap words in use) plus the 32-byte index
+    s->pool_bytes = (uint64_t)(mom[3] * 4.0) + 32ull * p->T;
+    s->raw_int32_bytes = 4ull * p->hc.rr_vertices + 8ull * p->T;
+    if (p->T) {
+        const double T = (double)p->T, mean = mom[0] / T;
+        const double m2 = mom[1] / T - mean * mean;
+        const double m3 = mom[2] / T - 3 * mean * mom[1] / T + 2 * mean * mean * mean;
+        s->skewness = m2 > 0 ? m3 / (m2 * std::sqrt(m2)) : 0.0;
+        s->density = mom[0] / (T * (double)p->g->n);
+    }
+    s->sample_s = p->sample_s;
+    s->select_s = p->select_s;
+    s->sample_kernel_s = p->sample_kernel_s;
+    s->sample_kernel_launches = p->sample_kernel_launches;
+    s->kernel_launches = p->launches;
+}
+
+int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds, double* influence,
+                uint64_t* marginal, hbx_stats* stats) {
+    hbx_ctx* ctx = p->ctx;
+    const double t0 = now_s();
+    const uint32_t n = p->g->n;
+    ImmBounds b;
+    if (!imm_bounds(n, k, eps, ell, &b)) return fail(ctx, HBX_ERR_INVALID_ARG, "bad k, eps, ell or n");
+    const double dn = (double)n;
+    if (p->o.encode && !p->has_cb && p->W == 0) {
+        const uint64_t T1 = (uint64_t)std::ceil(b.lambda_p / (dn / std::ldexp(1.0, 1)));
+        p->W = (T1 + 7) / 8;
+    }
+    std::vector<uint32_t> tmp(k);
+    uint64_t Ti = 0;
+    double LB = 1.0;
+    uint32_t rounds = 0;
+    const uint32_t imax = ilog2_floor(n) - 1;
+    for (uint32_t i = 1; i <= imax; i++) {
+        const double x = dn / std::ldexp(1.0, (int)i);
+        const uint64_t t = (uint64_t)std::ceil(b.lambda_p / x);
+        if (t > Ti) Ti = t;
+        RC(pool_extend(p, Ti));
+        uint64_t cov = 0;
+        RC(pool_select(p, Ti, k, tmp.data(), nullptr, &cov));
+        rounds++;
+        const double est = dn * (double)cov / (double)Ti;
+        if (est >= (1.0 + b.epsp) * x) {
+            LB = est / (1.0 + b.epsp);
+            break;
+        }
+    }
+    uint64_t T = (uint64_t)std::ceil(b.lambda_star / LB);
+    if (T < Ti) T = Ti;
+    RC(pool_extend(p, T));
+    uint64_t cov = 0;
+    RC(pool_select(p, T, k, seeds, marginal, &cov));
+    *influence = dn * (double)cov / (double)T;
+    if (stats) {
+        fill_stats(p, stats);
+        stats->theta = T;
+        stats->covered = cov;
+        stats->rounds = rounds;
+        stats->lb = LB;
+        stats->total_s = now_s() - t0;
+    }
+    return HBX_OK;
+}
+
+}  // namespace hbx
+
+extern "C" int hbx_imm_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds, double* influence,
+                            uint64_t* marginal, hbx_stats* stats) {
+    if (!p || !seeds || !influence) return HBX_ERR_INVALID_ARG;
+    return imm_on_pool(p, k, eps, ell, seeds, influence, marginal, stats);
+}
+
+extern "C" int hbx_imm(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint32_t k, double eps, double ell,
+                       uint64_t seed, const hbx_options* opts, uint32_t* seeds, double* influence,
+                       uint64_t* marginal, hbx_stats* stats) {
+    if (!ctx || !g || !seeds || !influence) return HBX_ERR_INVALID_ARG;
+    hbx_pool* p = nullptr;
+    RC(hbx_pool_create(ctx, g, model, seed, opts, &p));
+    const int r = imm_on_pool(p, k, eps, ell, seeds, influence, marginal, stats);
+    hbx_pool_destroy(p);
+    return r;
+}
+
+// ===========================================================================
+// inspection
+// ===========================================================================
+extern "C" int hbx_pool_export_set(hbx_pool* p, uint64_t j, uint32_t* kind, uint32_t* size, uint32_t* n_coded,
+                                   uint32_t* n_raw, uint64_t* code_bits, uint8_t* payload, uint64_t cap,
+                                   uint64_t* nbytes) {
+    if (!p) return HBX_ERR_INVALID_ARG;
+    hbx_ctx* ctx = p->ctx;
+    if (j >= p->T) return fail(ctx, HBX_ERR_INVALID_ARG, "set id beyond the pool");
+    cudaSetDevice(ctx->device);
+    SetRec r;
+    CK(cudaMemcpyAsync(&r, p->recs + j, sizeof(r), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (kind) *kind = r.kind;
+    if (size) *size = r.size;
+    if (n_coded) *n_coded = r.kind == KIND_HUFF ? r.n_coded : 0;
+    if (n_raw) *n_raw = r.kind == KIND_HUFF ? r.size - r.n_coded : 0;
+    if (code_bits) *code_bits = r.kind == KIND_HUFF ? r.code_bits : 0;
+    std::vector<uint8_t> buf;
+    if (r.kind == KIND_HUFF) {
+        const uint32_t nside = r.n_coded ? (r.n_coded - 1) / 32 : 0;
+        const uint64_t cb = (r.code_bits + 7) / 8, cw = (r.code_bits + 31) / 32;
+        const uint64_t raw_at = (cb + 3) & ~3ull;
+        const uint32_t nr = r.size - r.n_coded;
+        buf.assign(raw_at + 4ull * nr, 0);
+        std::vector<uint32_t> words(cw + 1);
+        if (cw) CK(cudaMemcpyAsync(words.data(), p->code.d + r.off + nside, cw * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        if (nr) CK(cudaMemcpyAsync(buf.data() + raw_at, p->raw.d + r.raw_off, 4ull * nr, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        memcpy(buf.data(), words.data(), cb);
+    } else if (r.kind == KIND_BITMAP) {
+        const uint64_t nw = ((uint64_t)p->g->n + 31) / 32;
+        buf.resize(nw * 4);
+        CK(cudaMemcpyAsync(buf.data(), p->bm.d + r.off, nw * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else if (r.kind == KIND_RAW) {
+        buf.resize(4ull * r.size);
+        CK(cudaMemcpyAsync(buf.data(), p->raw.d + r.off, 4ull * r.size, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        return fail(ctx, HBX_ERR_INTERNAL, "set not written");
+    }
+    if (nbytes) *nbytes = buf.size();
+    if (buf.size() > cap || (!payload && buf.size()))
+        return fail(ctx, HBX_ERR_INVALID_ARG, "payload buffer too small");
+    if (buf.size()) memcpy(payload, buf.data(), buf.size());
+    return HBX_OK;
+}
+
+extern "C" int hbx_pool_decode_sets(hbx_pool* p, uint64_t j0, uint64_t j1, uint64_t* offsets, uint32_t* verts,
+                                    uint64_t cap, uint64_t* needed) {
+    if (!p || !offsets) return HBX_ERR_INVALID_ARG;
+    hbx_ctx* ctx = p->ctx;
+    if (j0 > j1 || j1 > p->T) return fail(ctx, HBX_ERR_INVALID_ARG, "range beyond the pool");
+    cudaSetDevice(ctx->device);
+    const uint64_t cnt = j1 - j0;
+    std::vector<SetRec> recs(cnt);
+    if (cnt) CK(cudaMemcpyAsync(recs.data(), p->recs + j0, cnt * sizeof(SetRec), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    offsets[0] = 0;
+    for (uint64_t i = 0; i < cnt; i++) offsets[i + 1] = offsets[i] + recs[i].size;
+    if (needed) *needed = offsets[cnt];
+    if (offsets[cnt] > cap || (!verts && offsets[cnt])) return fail(ctx, HBX_ERR_INVALID_ARG, "verts buffer too small");
+    if (!cnt) return HBX_OK;
+    unsigned long long* d_off = nullptr;
+    uint32_t* d_out = nullptr;
+    RC(dalloc(ctx, (void**)&d_off, (cnt + 1) * 8));
+    int r = dalloc(ctx, (void**)&d_out, std::max<uint64_t>(offsets[cnt], 1) * 4);
+    if (r) {
+        dfree(ctx, d_off);
+        return r;
+    }
+    DecodeArgs a;
+    a.recs = p->recs;
+    a.raw_heap = p->raw.d;
+    a.code_heap = p->code.d;
+    a.bm_heap = p->bm.d;
+    a.cb = dev_codebook(p);
+    a.has_cb = p->has_cb;
+    a.n = p->g->n;
+    a.j0 = (uint32_t)j0;
+    a.j1 = (uint32_t)j1;
+    a.offsets = d_off;
+    a.out = d_out;
+    a.ctr = p->ctr;
+    cudaError_t e = cudaMemcpyAsync(d_off, offsets, (cnt + 1) * 8, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_decode(a, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(verts, d_out, offsets[cnt] * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, d_off);
+    dfree(ctx, d_out);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "decode");
+    RC(read_counters(p));
+    for (uint64_t i = 0; i < cnt; i++) std::sort(verts + offsets[i], verts + offsets[i + 1]);
+    return HBX_OK;
+}
+
+extern "C" int hbx_pool_export_codebook(hbx_pool* p, uint32_t* len_of_v, uint32_t* code_of_v, uint32_t* rank_of_v,
+                                        uint32_t* freq) {
+    if (!p) return HBX_ERR_INVALID_ARG;
+    if (!p->has_cb) return fail(p->ctx, HBX_ERR_INVALID_ARG, "pool has no codebook");
+    const uint32_t n = p->g->n;
+    if (len_of_v) memcpy(len_of_v, p->h_len.data(), (size_t)n * 4);
+    if (code_of_v) memcpy(code_of_v, p->h_code.data(), (size_t)n * 4);
+    if (rank_of_v) memcpy(rank_of_v, p->h_rank.data(), (size_t)n * 4);
+    if (freq) memcpy(freq, p->h_freq.data(), (size_t)n * 4);
+    return HBX_OK;
+}
+
+extern "C" int hbx_pool_stats(hbx_pool* p, hbx_stats* s) {
+    if (!p || !s) return HBX_ERR_INVALID_ARG;
+    cudaSetDevice(p->ctx->device);
+    fill_stats(p, s);
+    return HBX_OK;
+}

@@ -1,0 +1,119 @@
+// Host-side objects behind the opaque handles of include/hbx.h.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <thread>
+#include <utility>
+#include <vector>
+
+#include "hbx.h"
+#include "internal.h"
+
+struct hbx_ctx {
+    int device = 0;
+    int sms = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* (*alloc_fn)(size_t, void*) = nullptr;
+    void (*free_fn)(void*, void*) = nullptr;
+    void* alloc_user = nullptr;
+    std::string last_error;
+    std::map<void*, size_t> sizes;  // live device allocations
+    size_t live_bytes = 0;
+    std::set<hbx_graph*> graphs;
+    std::set<hbx_pool*> pools;
+    std::set<hbx_server*> servers;
+    std::map<std::pair<const hbx_graph*, int>, uint32_t> tuned;  // autotuned warp capacity
+    std::mutex mu;  // guards allocation bookkeeping when a server worker runs
+};
+
+struct hbx_graph {
+    hbx_ctx* ctx = nullptr;
+    uint32_t n = 0, m = 0;
+    uint32_t max_indeg = 0;
+    uint32_t* row_ptr = nullptr;
+    uint32_t* col = nullptr;
+    float* prob = nullptr;  // 4*ceil(m/4) floats
+    uint32_t* q = nullptr;  // LT fixed-point weights
+};
+
+namespace hbx {
+struct Heap {
+    uint32_t* d = nullptr;
+    uint64_t cap = 0;  // words usable (the allocation has slack words beyond)
+};
+}  // namespace hbx
+
+struct hbx_pool {
+    hbx_ctx* ctx = nullptr;
+    hbx_graph* g = nullptr;
+    hbx_model model = HBX_IC;
+    uint64_t seed = 0;
+    hbx_options o{};
+    uint64_t T = 0;
+    uint32_t qw = 0;
+    size_t device_bytes = 0;
+    hbx::SetRec* recs = nullptr;
+    uint64_t rec_cap = 0;
+    hbx::Heap raw, code, bm;
+    hbx::Counters* ctr = nullptr;
+    hbx::Counters hc{};
+    double* moments = nullptr;
+    unsigned long long aux_scanned = 0, aux_live = 0;  // edges of warm-up/calibration passes
+    // codebook
+    bool has_cb = false;
+    uint64_t W = 0;
+    uint32_t nsym = 0, max_len = 0;
+    uint32_t *rank_of = nullptr, *vertex_of_rank = nullptr, *code_of_rank = nullptr, *lut = nullptr, *dec = nullptr;
+    uint8_t* len_of_rank = nullptr;
+    std::vector<uint32_t> h_freq, h_len, h_code, h_rank;
+    // selection index
+    unsigned long long* items = nullptr;
+    uint64_t items_cap = 0;
+    uint32_t* bm_sets = nullptr;
+    uint64_t bm_list_cap = 0;
+    // sampling lists
+    uint32_t *big_list = nullptr, *retry_list = nullptr, *list_in = nullptr;
+    uint64_t list_cap = 0;
+    // block-path scratch
+    uint32_t *bp_visited = nullptr, *bp_rbits = nullptr, *bp_aux = nullptr, *bp_queue = nullptr;
+    uint32_t bp_slots = 0;
+    uint64_t bp_words = 0;
+    // selection state
+    int32_t* cnt = nullptr;
+    uint8_t* alive = nullptr;
+    uint64_t alive_cap = 0;
+    uint32_t *cov_huff = nullptr, *cov_bm = nullptr, *cov_raw = nullptr;
+    void* st = nullptr;
+    unsigned long long* partials = nullptr;
+    unsigned int* ticket = nullptr;
+    uint32_t* d_seeds = nullptr;
+    unsigned long long* d_marg = nullptr;
+    uint32_t kcap = 0;
+    double sample_s = 0, select_s = 0;
+    double sample_kernel_s = 0;
+    uint64_t sample_kernel_launches = 0;
+    uint64_t launches = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace hbx {
+int fail(hbx_ctx* c, int code, const std::string& msg);
+int cuda_fail(hbx_ctx* c, cudaError_t e, const char* what);
+int dalloc(hbx_ctx* c, void** p, size_t bytes);
+void dfree(hbx_ctx* c, void* p);
+int pool_extend(hbx_pool* p, uint64_t T);
+int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* marginal, uint64_t* covered);
+int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds, double* influence,
+                uint64_t* marginal, hbx_stats* stats);
+void fill_stats(hbx_pool* p, hbx_stats* s);
+}  // namespace hbx
+
+void hbx_server_destroy_all(hbx_ctx* c);

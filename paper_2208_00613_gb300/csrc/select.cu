@@ -1,0 +1,535 @@
+// Greedy max-coverage seed selection on the encoded RR pool (Section 2.2;
+// Section 4.3, Algorithms 2 and 3), without materialising decoded sets.
+//
+// State: cnt[v] = number of uncovered sets holding v (int32; -1 marks a chosen
+// vertex and the padding up to a multiple of 4), alive[j] = set j not yet
+// covered.  One iteration:
+//   argmax     u* = the vertex with the largest cnt, lowest id on ties (an exact
+//              reduction; the paper's per-thread "parallel merge" of Section
+//              4.3.4 can miss the true maximum and is not used);
+//   cover      every alive set holding u* is marked covered: Huffman sets decode
+//              only until a rank >= rank(u*) (codes are in ascending rank, and a
+//              side index of chunk offsets allows a binary search), or search
+//              their sorted copy array; bitmaps test one bit (Algorithm 3's
+//              row of u*);
+//   decrement  the covered sets' vertices lose one count: Huffman sets are
+//              decoded in 32-code chunks, bitmaps are summed per vertex with
+//              bit-plane counters (the SUBTRACT + POPCOUNT of Eq. (3));
+//   finalize   record u*, its marginal gain, and mark it chosen.
+// Counts are exact u32 integers (the paper's float table is not needed).
+#include "common.cuh"
+#include "internal.h"
+
+namespace hbx {
+
+constexpr int SEL_THREADS = 256;
+constexpr int COUNT_THREADS = 512;
+constexpr uint32_t HOT_MAX = 12288;  // ranks privatised in shared memory (48 KB)
+constexpr uint32_t BM_BATCH = 255;   // bitmap sets per bit-plane flush
+
+SelShape sel_shape(int sms) {
+    SelShape s;
+    s.count_blocks = (uint32_t)sms * 2;
+    s.argmax_blocks = (uint32_t)sms * 2;
+    s.cover_blocks = (uint32_t)sms * 4;
+    s.dec_blocks = (uint32_t)sms * 4;
+    return s;
+}
+
+__global__ void sel_init_kernel(SelArgs a) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n4; v += stride) a.cnt[v] = v < a.n ? 0 : -1;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < a.T; j += stride) a.alive[j] = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        SelState z;
+        z.u = NONE; z.it = 0; z.n_cov_huff = 0; z.n_cov_bm = 0; z.n_cov_raw = 0; z.pad = 0; z.gain = 0; z.covered = 0;
+        *a.st = z;
+        *a.ticket = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial count over Huffman chunks: one thread decodes one 32-code chunk (or
+// copies 32 copy-array ids).  Hot ranks go to a shared-memory histogram, the
+// rest to cnt with one atomic per group of lanes hitting the same vertex.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(COUNT_THREADS) count_huff_kernel(SelArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    DecodeSmem& ds = *reinterpret_cast<DecodeSmem*>(smem);
+    uint32_t* hist = smem + sizeof(DecodeSmem) / 4;
+    load_decode_smem(ds, a.cb);
+    for (uint32_t i = threadIdx.x; i < a.hot; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long wb = (unsigned long long)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+         wb < a.n_items; wb += nwarps * 32) {
+        const unsigned long long t = wb + lane;
+        uint32_t ncodes = 0, is_code = 0;
+        uint64_t pos = 0;
+        const uint32_t* words = nullptr;
+        const uint32_t* raw = nullptr;
+        if (t < a.n_items) {
+            const unsigned long long item = a.chunk_items[t];
+            const uint32_t j = (uint32_t)(item >> 32), c = (uint32_t)item;
+            if (j < a.T) {
+                const SetRec rec = a.recs[j];
+                const uint32_t nch = (rec.n_coded + 31) / 32;
+                if (c < nch) {
+                    const uint32_t nside = (rec.n_coded - 1) / 32;
+                    words = a.code_heap + rec.off + nside;
+                    pos = c ? a.code_heap[rec.off + c - 1] : 0u;
+                    ncodes = min(32u, rec.n_coded - 32 * c);
+                    is_code = 1;
+                } else {
+                    const uint32_t rc = c - nch;
+                    const uint32_t n_raw = rec.size - rec.n_coded;
+                    raw = a.raw_heap + rec.raw_off + 32ull * rc;
+                    ncodes = min(32u, n_raw - 32 * rc);
+                }
+            }
+        }
+        for (uint32_t i = 0; i < 32; i++) {
+            const bool have = i < ncodes;
+            uint32_t target = NONE;
+            if (have) {
+                if (is_code) {
+                    const uint32_t r = decode_one(ds, words, pos);
+                    if (r == NONE) atomicMax(&a.st->pad, 1u);
+                    else target = r < a.hot ? r : (RAW_FLAG | __ldg(a.cb.vertex_of_rank + r));
+                } else {
+                    target = RAW_FLAG | raw[i];
+                }
+            }
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, target);
+            if (have && target != NONE && lane == (uint32_t)(__ffs(peers) - 1)) {
+                const uint32_t c = __popc(peers);
+                if (target & RAW_FLAG) atomicAdd(&a.cnt[target & ~RAW_FLAG], (int)c);
+                else atomicAdd(&hist[target], c);
+            }
+            if (__all_sync(0xFFFFFFFFu, i + 1 >= ncodes)) break;
+        }
+    }
+    __syncthreads();
+    for (uint32_t r = threadIdx.x; r < a.hot; r += blockDim.x) {
+        const uint32_t h = hist[r];
+        if (h) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], (int)h);
+    }
+}
+
+// Per-vertex sums over bitmap rows: thread (word w, batch b) adds word w of
+// each listed set in its batch into 8 bit-planes (a ripple-carry adder per bit
+// position), then adds sign * count to cnt[32w + bit].
+__global__ void bitmap_count_kernel(SelArgs a, const uint32_t* list, const uint32_t* list_len_dev,
+                                    uint32_t list_len_host, int sign, int check_alive) {
+    const uint32_t nw = (a.n + 31) / 32;
+    const uint64_t row = (((uint64_t)a.n + 31) / 32 + 3) & ~3ull;
+    const uint32_t len = list_len_dev ? *list_len_dev : list_len_host;
+    const uint32_t nbatch = (len + BM_BATCH - 1) / BM_BATCH;
+    const uint64_t total = (uint64_t)nw * nbatch;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = (uint32_t)(t % nw), b = (uint32_t)(t / nw);
+        const uint32_t s0 = b * BM_BATCH, s1 = min(len, s0 + BM_BATCH);
+        uint32_t p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t s = s0; s < s1; s++) {
+            const uint32_t j = list[s];
+            if (j >= a.T) continue;
+            if (check_alive && !a.alive[j]) continue;
+            const SetRec& rec = a.recs[j];
+            uint32_t c = __ldg(a.bm_heap + rec.off + w);
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const uint32_t t2 = p[i] & c;
+                p[i] ^= c;
+                c = t2;
+            }
+        }
+        (void)row;
+        const uint32_t any = p[0] | p[1] | p[2] | p[3] | p[4] | p[5] | p[6] | p[7];
+        if (!any) continue;
+        for (uint32_t bit = 0; bit < 32; bit++) {
+            if (!(any >> bit & 1u)) continue;
+            uint32_t c = 0;
+#pragma unroll
+            for (int i = 0; i < 8; i++) c |= ((p[i] >> bit) & 1u) << i;
+            const uint32_t v = w * 32 + bit;
+            if (c && v < a.n) atomicAdd(&a.cnt[v], sign * (int)c);
+        }
+    }
+}
+
+// Uncompressed pools: one warp per set.
+__global__ void count_raw_kernel(SelArgs a) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < a.T; j += nwarps) {
+        const SetRec rec = a.recs[j];
+        for (uint32_t i = lane; i < rec.size; i += 32) atomicAdd(&a.cnt[a.raw_heap[rec.off + i]], 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// argmax: key = (cnt + 1) << 32 | (2^32 - 1 - v); the largest key is the
+// largest count with the lowest id.  Chosen vertices (cnt = -1) get key high
+// word 0 and never win while an unchosen vertex exists.  The last block to
+// finish reduces the per-block results.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SEL_THREADS) argmax_kernel(SelArgs a) {
+    __shared__ unsigned long long s_w[SEL_THREADS / 32];
+    __shared__ bool s_last;
+    unsigned long long best = 0;
+    const uint32_t n4q = a.n4 / 4;
+    const int4* c4 = reinterpret_cast<const int4*>(a.cnt);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n4q; i += gridDim.x * blockDim.x) {
+        const int4 c = c4[i];
+        const uint32_t v = i * 4;
+        unsigned long long k0 = ((unsigned long long)(uint32_t)(c.x + 1) << 32) | (0xFFFFFFFFu - v);
+        unsigned long long k1 = ((unsigned long long)(uint32_t)(c.y + 1) << 32) | (0xFFFFFFFFu - (v + 1));
+        unsigned long long k2 = ((unsigned long long)(uint32_t)(c.z + 1) << 32) | (0xFFFFFFFFu - (v + 2));
+        unsigned long long k3 = ((unsigned long long)(uint32_t)(c.w + 1) << 32) | (0xFFFFFFFFu - (v + 3));
+        k0 = k0 > k1 ? k0 : k1;
+        k2 = k2 > k3 ? k2 : k3;
+        k0 = k0 > k2 ? k0 : k2;
+        best = best > k0 ? best : k0;
+    }
+    best = warp_max_u64(best);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long x = threadIdx.x < SEL_THREADS / 32 ? s_w[threadIdx.x] : 0ull;
+        x = warp_max_u64(x);
+        if (threadIdx.x == 0) {
+            a.partials[blockIdx.x] = x;
+            __threadfence();
+            const unsigned int t = atomicAdd(a.ticket, 1u);
+            s_last = (t == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned long long x = 0;
+    for (uint32_t i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+        const unsigned long long y = __ldcg(a.partials + i);
+        x = x > y ? x : y;
+    }
+    x = warp_max_u64(x);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0;
+        for (int i = 0; i < SEL_THREADS / 32; i++) m = m > s_w[i] ? m : s_w[i];
+        const uint32_t u = 0xFFFFFFFFu - (uint32_t)m;
+        a.st->u = u;
+        a.seeds[a.st->it] = u;
+        *a.ticket = 0;
+    }
+}
+
+// Membership of rank ru in a Huffman set: binary search on the first code of
+// each 32-code chunk, then a scan of one chunk, stopping at the first rank >= ru.
+__device__ bool huff_contains(const DecodeSmem& ds, const uint32_t* __restrict__ code_heap, const SetRec& rec,
+                              uint32_t ru) {
+    const uint32_t n = rec.n_coded;
+    if (n == 0) return false;
+    const uint32_t nside = (n - 1) / 32;
+    const uint32_t* words = code_heap + rec.off + nside;
+    uint32_t lo = 0, hi = nside;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        uint64_t pos = __ldg(code_heap + rec.off + mid - 1);
+        const uint32_t r = decode_one(ds, words, pos);
+        if (r <= ru) lo = mid;
+        else hi = mid - 1;
+    }
+    uint64_t pos = lo ? __ldg(code_heap + rec.off + lo - 1) : 0u;
+    const uint32_t cnt = min(32u, n - 32 * lo);
+    for (uint32_t i = 0; i < cnt; i++) {
+        const uint32_t r = decode_one(ds, words, pos);
+        if (r >= ru) return r == ru;
+    }
+    return false;
+}
+
+__device__ bool sorted_contains(const uint32_t* __restrict__ x, uint32_t len, uint32_t u) {
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t y = __ldg(x + mid);
+        if (y < u) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < len && __ldg(x + lo) == u;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) cover_kernel(SelArgs a) {
+    __shared__ DecodeSmem ds;
+    if (a.has_cb) load_decode_smem(ds, a.cb);
+    __syncthreads();
+    const uint32_t u = a.st->u;
+    const uint32_t ru = a.has_cb ? __ldg(a.cb.rank_of + u) : NONE;
+    unsigned long long gain = 0;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < a.T; j += gridDim.x * blockDim.x) {
+        if (!a.alive[j]) continue;
+        const SetRec rec = a.recs[j];
+        bool member = false;
+        if (rec.kind == KIND_HUFF) {
+            if (ru != NONE) member = huff_contains(ds, a.code_heap, rec, ru);
+            else member = sorted_contains(a.raw_heap + rec.raw_off, rec.size - rec.n_coded, u);
+        } else if (rec.kind == KIND_BITMAP) {
+            member = (__ldg(a.bm_heap + rec.off + (u >> 5)) >> (u & 31)) & 1u;
+        } else {
+            for (uint32_t i = 0; i < rec.size && !member; i++) member = __ldg(a.raw_heap + rec.off + i) == u;
+        }
+        if (member) {
+            a.alive[j] = 0;
+            gain++;
+            if (rec.kind == KIND_HUFF) a.cov_huff[atomicAdd(&a.st->n_cov_huff, 1u)] = j;
+            else if (rec.kind == KIND_BITMAP) a.cov_bm[atomicAdd(&a.st->n_cov_bm, 1u)] = j;
+            else a.cov_raw[atomicAdd(&a.st->n_cov_raw, 1u)] = j;
+        }
+    }
+    gain = (unsigned long long)warp_sum((uint32_t)gain);
+    if ((threadIdx.x & 31) == 0 && gain) atomicAdd(&a.st->gain, gain);
+}
+
+// Covered Huffman sets: one warp per set, lanes over 32-code chunks.
+__global__ void __launch_bounds__(SEL_THREADS) dec_huff_kernel(SelArgs a) {
+    __shared__ DecodeSmem ds;
+    load_decode_smem(ds, a.cb);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t len = a.st->n_cov_huff;
+    for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += nwarps) {
+        const SetRec rec = a.recs[a.cov_huff[i]];
+        const uint32_t n = rec.n_coded;
+        const uint32_t nch = (n + 31) / 32;
+        const uint32_t nside = n ? (n - 1) / 32 : 0;
+        const uint32_t* words = a.code_heap + rec.off + nside;
+        for (uint32_t c = lane; c < nch; c += 32) {
+            uint64_t pos = c ? __ldg(a.code_heap + rec.off + c - 1) : 0u;
+            const uint32_t cnt = min(32u, n - 32 * c);
+            for (uint32_t k = 0; k < cnt; k++) {
+                const uint32_t r = decode_one(ds, words, pos);
+                if (r != NONE) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -1);
+            }
+        }
+        const uint32_t n_raw = rec.size - n;
+        for (uint32_t k = lane; k < n_raw; k += 32) atomicAdd(&a.cnt[__ldg(a.raw_heap + rec.raw_off + k)], -1);
+    }
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) dec_raw_kernel(SelArgs a) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t len = a.st->n_cov_raw;
+    for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += nwarps) {
+        const SetRec rec = a.recs[a.cov_raw[i]];
+        for (uint32_t k = lane; k < rec.size; k += 32) atomicAdd(&a.cnt[__ldg(a.raw_heap + rec.off + k)], -1);
+    }
+}
+
+__global__ void finalize_kernel(SelArgs a) {
+    SelState s = *a.st;
+    a.cnt[s.u] = -1;
+    a.marginal[s.it] = s.gain;
+    s.covered += s.gain;
+    s.gain = 0;
+    s.it++;
+    s.n_cov_huff = 0;
+    s.n_cov_bm = 0;
+    s.n_cov_raw = 0;
+    *a.st = s;
+}
+
+cudaError_t launch_sel_init(const SelArgs& a, cudaStream_t s) {
+    const uint32_t work = a.n4 > a.T ? a.n4 : a.T;
+    uint32_t blocks = (work + SEL_THREADS - 1) / SEL_THREADS;
+    const uint32_t cap = (uint32_t)a.sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    sel_init_kernel<<<blocks, SEL_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const SelArgs& a, uint32_t encode, cudaStream_t s) {
+    const SelShape sh = sel_shape(a.sms);
+    if (!encode) {
+        count_raw_kernel<<<sh.count_blocks * 2, SEL_THREADS, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    if (a.n_items && a.has_cb) {
+        const size_t smem = sizeof(DecodeSmem) + (size_t)a.hot * 4;
+        cudaError_t e = cudaFuncSetAttribute(count_huff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        count_huff_kernel<<<sh.count_blocks, COUNT_THREADS, smem, s>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (a.n_bm) {
+        bitmap_count_kernel<<<sh.count_blocks * 2, SEL_THREADS, 0, s>>>(a, a.bm_sets, nullptr, a.n_bm, 1, 0);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_argmax(const SelArgs& a, cudaStream_t s) {
+    const SelShape sh = sel_shape(a.sms);
+    argmax_kernel<<<sh.argmax_blocks, SEL_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iteration(const SelArgs& a, uint32_t encode, cudaStream_t s) {
+    const SelShape sh = sel_shape(a.sms);
+    argmax_kernel<<<sh.argmax_blocks, SEL_THREADS, 0, s>>>(a);
+    cover_kernel<<<sh.cover_blocks, SEL_THREADS, 0, s>>>(a);
+    if (encode) {
+        if (a.has_cb) dec_huff_kernel<<<sh.dec_blocks, SEL_THREADS, 0, s>>>(a);
+        if (a.n_bm)
+            bitmap_count_kernel<<<sh.dec_blocks, SEL_THREADS, 0, s>>>(a, a.cov_bm, &a.st->n_cov_bm, 0, -1, 0);
+    } else {
+        dec_raw_kernel<<<sh.dec_blocks, SEL_THREADS, 0, s>>>(a);
+    }
+    finalize_kernel<<<1, 1, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Pool indexing after sampling: Huffman sets contribute one work item per 32
+// codes or 32 copy-array ids; bitmap sets are listed.  Also the size moments of
+// Eq. (2).
+// ---------------------------------------------------------------------------
+__global__ void index_kernel(IndexArgs a) {
+    __shared__ double s_m[4][SEL_THREADS / 32];
+    double m1 = 0, m2 = 0, m3 = 0, m4 = 0;
+    const uint64_t row = (((uint64_t)a.n + 31) / 32 + 3) & ~3ull;
+    for (uint32_t j = a.j0 + blockIdx.x * blockDim.x + threadIdx.x; j < a.j1; j += gridDim.x * blockDim.x) {
+        const SetRec rec = a.recs[j];
+        if (rec.kind == KIND_PENDING) {
+            atomicMax(&a.ctr->error, 3ull);
+            continue;
+        }
+        const double x = (double)rec.size;
+        m1 += x;
+        m2 += x * x;
+        m3 += x * x * x;
+        if (rec.kind == KIND_HUFF)
+            m4 += (double)((rec.n_coded ? (rec.n_coded - 1) / 32 : 0) + (rec.code_bits + 31) / 32 +
+                           (rec.size - rec.n_coded));
+        else if (rec.kind == KIND_BITMAP)
+            m4 += (double)row;
+        else
+            m4 += x;
+        if (rec.kind == KIND_HUFF) {
+            const uint32_t nch = (rec.n_coded + 31) / 32 + (rec.size - rec.n_coded + 31) / 32;
+            const unsigned long long base = atomicAdd(&a.ctr->chunk_items, (unsigned long long)nch);
+            if (base + nch > a.items_cap) {
+                atomicMax(&a.ctr->error, 4ull);
+                continue;
+            }
+            for (uint32_t c = 0; c < nch; c++) a.chunk_items[base + c] = ((unsigned long long)j << 32) | c;
+        } else if (rec.kind == KIND_BITMAP) {
+            const unsigned long long b = atomicAdd(&a.ctr->bm_list, 1ull);
+            if (b >= a.bm_cap) {
+                atomicMax(&a.ctr->error, 4ull);
+                continue;
+            }
+            a.bm_sets[b] = j;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        m1 += __shfl_xor_sync(0xFFFFFFFFu, m1, d);
+        m2 += __shfl_xor_sync(0xFFFFFFFFu, m2, d);
+        m3 += __shfl_xor_sync(0xFFFFFFFFu, m3, d);
+        m4 += __shfl_xor_sync(0xFFFFFFFFu, m4, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_m[0][threadIdx.x >> 5] = m1;
+        s_m[1][threadIdx.x >> 5] = m2;
+        s_m[2][threadIdx.x >> 5] = m3;
+        s_m[3][threadIdx.x >> 5] = m4;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0;
+        for (int i = 0; i < SEL_THREADS / 32; i++) t += s_m[threadIdx.x][i];
+        if (t != 0) atomicAdd(&a.moments[threadIdx.x], t);
+    }
+}
+
+cudaError_t launch_index(const IndexArgs& a, cudaStream_t s) {
+    if (a.j1 <= a.j0) return cudaSuccess;
+    uint32_t blocks = (a.j1 - a.j0 + SEL_THREADS - 1) / SEL_THREADS;
+    if (blocks > 1024) blocks = 1024;
+    index_kernel<<<blocks, SEL_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Decode sets [j0, j1) to vertex lists (one warp per set), for inspection.
+// Huffman: vertices in rank order then the copy array; bitmap: ascending;
+// raw: as stored.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SEL_THREADS) decode_kernel(DecodeArgs a) {
+    __shared__ DecodeSmem ds;
+    if (a.has_cb) load_decode_smem(ds, a.cb);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t j = a.j0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < a.j1; j += nwarps) {
+        const SetRec rec = a.recs[j];
+        uint32_t* out = a.out + a.offsets[j - a.j0];
+        if (rec.kind == KIND_HUFF) {
+            const uint32_t n = rec.n_coded;
+            const uint32_t nch = (n + 31) / 32;
+            const uint32_t nside = n ? (n - 1) / 32 : 0;
+            const uint32_t* words = a.code_heap + rec.off + nside;
+            for (uint32_t c = lane; c < nch; c += 32) {
+                uint64_t pos = c ? a.code_heap[rec.off + c - 1] : 0u;
+                const uint32_t cnt = min(32u, n - 32 * c);
+                for (uint32_t k = 0; k < cnt; k++) {
+                    const uint32_t r = decode_one(ds, words, pos);
+                    if (r == NONE) {
+                        atomicMax(&a.ctr->error, 5ull);
+                        out[32 * c + k] = NONE;
+                    } else {
+                        out[32 * c + k] = a.cb.vertex_of_rank[r];
+                    }
+                }
+                if (c == nch - 1 && pos != rec.code_bits) atomicMax(&a.ctr->error, 6ull);
+            }
+            for (uint32_t k = lane; k < rec.size - n; k += 32) out[n + k] = a.raw_heap[rec.raw_off + k];
+        } else if (rec.kind == KIND_BITMAP) {
+            const uint32_t nw = (a.n + 31) / 32;
+            uint32_t base = 0;
+            for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
+                const uint32_t w = w0 + lane;
+                uint32_t x = w < nw ? a.bm_heap[rec.off + w] : 0u;
+                const uint32_t c = __popc(x);
+                const uint32_t incl = warp_incl_scan(c);
+                uint32_t p = base + incl - c;
+                while (x) {
+                    const uint32_t b = __ffs(x) - 1;
+                    out[p++] = w * 32 + b;
+                    x &= x - 1;
+                }
+                base += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            }
+        } else {
+            for (uint32_t k = lane; k < rec.size; k += 32) out[k] = a.raw_heap[rec.off + k];
+        }
+    }
+}
+
+cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
+    if (a.j1 <= a.j0) return cudaSuccess;
+    uint32_t blocks = (a.j1 - a.j0 + 7) / 8;
+    if (blocks > 2048) blocks = 2048;
+    decode_kernel<<<blocks, SEL_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace hbx
