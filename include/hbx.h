@@ -80,6 +80,13 @@ typedef struct {
     /* Largest set one warp samples in shared memory (power of two, 64..2048);
      * bigger sets go to a block per set.  0 lets the autotuner choose. */
     uint32_t warp_capacity;
+    /* Edge groups (4 consecutive in-edges) a warp may scan for one set before
+     * the set moves to a block; 0 = 2048 when warp_capacity is given, else
+     * autotuned; 0xFFFFFFFF = no limit. */
+    uint32_t warp_group_budget;
+    /* Blocks of a thread-block cluster that search one heavy set together
+     * (1, 2, 4 or 8); 0 = 1 when warp_capacity is given, else autotuned. */
+    uint32_t block_cluster;
     /* Upper bound on the device bytes of one pool; 0 = no bound. */
     uint64_t max_device_bytes;
 } hbx_options;
@@ -98,6 +105,8 @@ typedef struct {
     uint64_t warmup_sets;      /* W used */
     uint32_t rounds;           /* IMM estimation rounds run */
     uint32_t warp_capacity;    /* launch shape used */
+    uint32_t warp_group_budget;
+    uint32_t block_cluster;
     double lb;                 /* IMM lower bound on OPT */
     double sample_s, select_s, total_s;
     double skewness, density;  /* Eq. (2) over the pool's set sizes */
@@ -118,7 +127,7 @@ const char *hbx_strerror(int code);
 const char *hbx_last_error(const hbx_ctx *ctx);
 
 /* Defaults: density_cut 32, warmup_sets 0 (auto), encode 1, form 1, epoch 0,
- * warp_capacity 0 (autotune), max_device_bytes 0. */
+ * warp_capacity 0 and warp_group_budget 0 (autotune), max_device_bytes 0. */
 void hbx_default_options(hbx_options *opts);
 
 /* Create a context on CUDA device `cuda_device`.  `cuda_stream` is a

@@ -36,6 +36,7 @@ class HbxError(RuntimeError):
 class hbx_options(ctypes.Structure):
     _fields_ = [("density_cut", ctypes.c_uint32), ("warmup_sets", ctypes.c_uint32), ("encode", ctypes.c_uint32),
                 ("form", ctypes.c_uint32), ("pool_epoch", ctypes.c_uint32), ("warp_capacity", ctypes.c_uint32),
+                ("warp_group_budget", ctypes.c_uint32), ("block_cluster", ctypes.c_uint32),
                 ("max_device_bytes", ctypes.c_uint64)]
 
 
@@ -43,7 +44,8 @@ class hbx_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in
                 ["theta", "covered", "sets_huffman", "sets_bitmap", "sets_raw", "sets_big", "rr_vertices",
                  "edges_scanned", "edges_live", "pool_bytes", "raw_int32_bytes", "code_bits", "warmup_sets"]] + \
-               [("rounds", ctypes.c_uint32), ("warp_capacity", ctypes.c_uint32)] + \
+               [("rounds", ctypes.c_uint32), ("warp_capacity", ctypes.c_uint32),
+                ("warp_group_budget", ctypes.c_uint32), ("block_cluster", ctypes.c_uint32)] + \
                [(f, ctypes.c_double) for f in ["lb", "sample_s", "select_s", "total_s", "skewness", "density",
                                                 "sample_kernel_s"]] + \
                [("sample_kernel_launches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]

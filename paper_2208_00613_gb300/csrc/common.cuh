@@ -3,19 +3,21 @@
 // Layout of an RR pool in HBM (one pool = the sets R_0, R_1, ... of one graph,
 // model, seed and epoch; Section 4.2, Algorithm 1 keeps the same per-block
 // structures C_i, CP_i, B_i):
-//   recs[j]     32-byte record of set j: size, kind, offsets into the heaps.
-//   code heap   32-bit words.  A Huffman set owns `nside + ceil(code_bits/32)`
-//               consecutive words: first nside = (n_coded-1)/32 side-index
-//               entries (the bit offset where code 32*c starts, c = 1..), then
-//               its code stream.  Stream word i holds stream bits [32i, 32i+32)
-//               most-significant first, stored byte-swapped so that memory
-//               bytes read as the MSB-first byte-string of Section 4.2.2.
-//   raw heap    32-bit vertex ids: the copy arrays CP_j of Huffman sets (sorted
-//               ids of vertices without a code), or whole sets of an
-//               uncompressed pool (sampling order).
+//   recs[j]     16-byte record of set j: kind and word offset into the heap of
+//               its kind, size, number of coded vertices.
+//   code heap   32-bit words.  A Huffman set owns one region of
+//               nside + n_raw + ceil(code_bits/32) words: first the side index
+//               (nside = (n_coded-1)/32 entries, the bit offset where code 32*c
+//               starts, c = 1..), then its copy array CP_j (ids of vertices
+//               without a code, ascending), then its code stream.  Stream word i
+//               holds stream bits [32i, 32i+32) most-significant first, stored
+//               byte-swapped so that memory bytes read as the MSB-first
+//               byte-string of Section 4.2.2.
 //   bitmap heap 32-bit words: a bitmap set owns ceil(n/32) words rounded up to a
 //               multiple of 4 (16-byte aligned rows); bit v = word v/32, bit v%32
 //               (Section 4.2.3).
+//   raw heap    32-bit vertex ids of the sets of an uncompressed pool, in
+//               sampling order.
 // Every heap is zero-filled when allocated and written once.
 #pragma once
 #include <cstdint>
@@ -27,20 +29,30 @@ constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t RAW_FLAG = 0x80000000u;  // sort key of a vertex without a code
 constexpr int LUT_BITS = 11;                // first-level Huffman decode table
 
-enum : uint32_t { KIND_HUFF = 0, KIND_BITMAP = 1, KIND_RAW = 2, KIND_PENDING = 0xFFu };
+enum : uint32_t { KIND_HUFF = 0, KIND_BITMAP = 1, KIND_RAW = 2, KIND_PENDING = 3 };
 enum : uint32_t { MODE_HIST = 0, MODE_RAW = 1, MODE_ENCODE = 2 };
 enum : uint32_t { MODEL_IC = 0, MODEL_LT = 1 };
 enum : uint32_t { STREAM_IC = 1, STREAM_LT = 2, STREAM_ROOT = 3 };
 
 struct SetRec {
+    uint64_t off_kind;  // kind << 62 | word offset into the heap of that kind
     uint32_t size;
     uint32_t n_coded;
-    uint32_t code_bits;
-    uint32_t kind;
-    uint64_t off;      // word offset in the code, bitmap or raw heap (by kind)
-    uint64_t raw_off;  // copy array offset in the raw heap (Huffman sets)
 };
-static_assert(sizeof(SetRec) == 32, "SetRec is 32 bytes");
+static_assert(sizeof(SetRec) == 16, "SetRec is 16 bytes");
+constexpr uint64_t OFF_MASK = (1ull << 62) - 1;
+
+__host__ __device__ __forceinline__ uint32_t rec_kind(const SetRec& r) { return (uint32_t)(r.off_kind >> 62); }
+__host__ __device__ __forceinline__ uint64_t rec_off(const SetRec& r) { return r.off_kind & OFF_MASK; }
+__host__ __device__ __forceinline__ SetRec make_rec(uint32_t kind, uint64_t off, uint32_t size, uint32_t n_coded) {
+    SetRec r;
+    r.off_kind = ((uint64_t)kind << 62) | off;
+    r.size = size;
+    r.n_coded = n_coded;
+    return r;
+}
+// side-index entries of a Huffman set with n_coded codes
+__host__ __device__ __forceinline__ uint32_t side_words(uint32_t n_coded) { return n_coded ? (n_coded - 1) / 32 : 0; }
 
 struct DevGraph {
     uint32_t n;
@@ -72,7 +84,8 @@ struct Counters {
     unsigned long long sets_huff, sets_bm, sets_raw, sets_big;
     unsigned long long error;
     unsigned long long chunk_items, bm_list;  // selection indexes
-    unsigned long long pad[13];
+    unsigned long long words_used;            // heap words held by emitted sets
+    unsigned long long pad[12];
 };
 
 struct SampleArgs {
@@ -82,6 +95,7 @@ struct SampleArgs {
     uint32_t j0, count;       // sets j0 .. j0+count-1, or list[0..count)
     const uint32_t* list;
     uint32_t persistent;      // 1: work stealing over a fixed grid; 0: one warp per set
+    uint32_t group_budget;    // 4-edge groups a warp may scan for one set before handing it to a block
     uint32_t* freq;           // MODE_HIST: warm-up vertex frequencies [n]
     SetRec* recs;
     uint32_t* raw_heap;
@@ -208,6 +222,28 @@ __device__ __forceinline__ uint32_t decode_one(const DecodeSmem& s, const uint32
         if (d < s.count[L]) {
             pos += L;
             return s.first_rank[L] + d;
+        }
+    }
+    return NONE;
+}
+
+// The same decoder reading the tables straight from global memory through the
+// read-only cache (for kernels that decode only a few codes per block).
+__device__ __forceinline__ uint32_t decode_one_g(const DevCodebook& cb, const uint32_t* __restrict__ words,
+                                                 uint64_t& pos) {
+    const uint32_t win = peek32(words, pos);
+    const uint32_t e = __ldg(cb.lut + (win >> (32 - LUT_BITS)));
+    uint32_t L = e & 63u;
+    if (L) {
+        pos += L;
+        return e >> 6;
+    }
+    for (L = LUT_BITS + 1; L <= 32; L++) {
+        const uint32_t c = L == 32 ? win : (win >> (32 - L));
+        const uint32_t d = c - __ldg(cb.dec + L);
+        if (d < __ldg(cb.dec + 33 + L)) {
+            pos += L;
+            return __ldg(cb.dec + 66 + L) + d;
         }
     }
     return NONE;

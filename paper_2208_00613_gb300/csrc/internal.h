@@ -10,8 +10,8 @@ namespace hbx {
 
 // ---- sampling (sample.cu) ----
 cudaError_t launch_sample_warp(const SampleArgs& a, uint32_t qw, int sms, cudaStream_t s);
-cudaError_t launch_sample_block(const SampleArgs& a, uint32_t nbig, uint32_t slots, cudaStream_t s);
-int block_path_threads();
+cudaError_t launch_sample_block(const SampleArgs& a, uint32_t nbig, uint32_t slots, uint32_t csize, cudaStream_t s);
+int block_path_max_clusters(uint32_t csize);
 
 // ---- selection (select.cu) ----
 struct SelState {
@@ -48,6 +48,8 @@ struct SelArgs {
     int sms;
 };
 
+constexpr uint32_t HOT_RANKS = 12288;  // ranks privatised in shared memory by the count kernel
+
 // Launch shapes used by the selection kernels (grids are fixed so that the k
 // iterations can be captured in one CUDA graph).
 struct SelShape {
@@ -70,8 +72,7 @@ struct IndexArgs {
     uint32_t* bm_sets;
     uint32_t bm_cap;
     Counters* ctr;
-    double* moments;  // [4]: sum |R|, |R|^2, |R|^3, heap words held by the sets
-    uint32_t n;
+    double* moments;  // [3]: sums of |R|, |R|^2, |R|^3
 };
 cudaError_t launch_index(const IndexArgs& a, cudaStream_t s);
 
@@ -86,6 +87,7 @@ struct DecodeArgs {
     uint32_t j0, j1;
     const unsigned long long* offsets;  // j1-j0+1, into out
     uint32_t* out;
+    unsigned long long* ends;           // j1-j0 bit positions after the last code, or null
     Counters* ctr;
 };
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);

@@ -116,6 +116,8 @@ extern "C" void hbx_default_options(hbx_options* o) {
     o->form = 1;
     o->pool_epoch = 0;
     o->warp_capacity = 0;
+    o->warp_group_budget = 0;
+    o->block_cluster = 0;
     o->max_device_bytes = 0;
 }
 
@@ -217,6 +219,26 @@ extern "C" int hbx_graph_create(hbx_ctx* ctx, uint32_t n, uint64_t m, const uint
     g->n = n;
     g->m = (uint32_t)m;
     g->max_indeg = max_deg;
+    {
+        // content fingerprint (FNV-1a over sizes and 64 sampled CSR entries)
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&](uint64_t x) {
+            for (int b = 0; b < 8; b++) {
+                h ^= (x >> (8 * b)) & 0xFF;
+                h *= 1099511628211ull;
+            }
+        };
+        mix(n);
+        mix(m);
+        for (uint32_t i = 0; i < 64; i++) {
+            const uint64_t v = (uint64_t)n * i / 64, e = m ? m * i / 64 : 0;
+            mix(row_ptr[v]);
+            if (m) mix(col[e]);
+            if (m && ic_prob) mix((uint64_t)(ic_prob[e] * 1e9f));
+            if (m && lt_weight) mix((uint64_t)(lt_weight[e] * 1e9f));
+        }
+        g->fingerprint = h;
+    }
     auto up = [&](void** dst, const void* src, size_t bytes, size_t alloc_bytes) -> int {
         int r = dalloc(ctx, dst, alloc_bytes);
         if (r) return r;
@@ -258,8 +280,6 @@ extern "C" void hbx_graph_destroy(hbx_graph* g) {
     dfree(c, g->prob);
     dfree(c, g->q);
     c->graphs.erase(g);
-    for (auto it = c->tuned.begin(); it != c->tuned.end();)
-        it = (it->first.first == g) ? c->tuned.erase(it) : std::next(it);
     delete g;
 }
 
@@ -335,7 +355,7 @@ static int ensure_recs(hbx_pool* p, uint64_t T) {
     uint64_t nc = std::max<uint64_t>(T, p->rec_cap * 2);
     nc = std::max<uint64_t>(nc, 4096);
     void* b = p->recs;
-    // new records are KIND_PENDING (0xFF bytes in kind) until written
+    // new records are KIND_PENDING (all-ones bytes: kind bits 3) until written
     hbx_ctx* ctx = p->ctx;
     RC(pool_bytes_check(p, (nc - p->rec_cap) * sizeof(SetRec)));
     void* nb = nullptr;
@@ -391,7 +411,7 @@ static int reset_launch_counters(hbx_pool* p) {
 }
 
 static SampleArgs sample_args(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, const uint32_t* list,
-                              uint32_t* freq, uint32_t cut) {
+                              uint32_t* freq, uint32_t cut, const Shape& sh) {
     SampleArgs a;
     memset(&a, 0, sizeof(a));
     a.g = dev_graph(p->g);
@@ -405,6 +425,7 @@ static SampleArgs sample_args(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t 
     a.count = count;
     a.list = list;
     a.persistent = p->o.form ? 1u : 0u;
+    a.group_budget = sh.gb;
     a.freq = freq;
     a.recs = p->recs;
     a.raw_heap = p->raw.d;
@@ -428,16 +449,16 @@ static SampleArgs sample_args(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t 
 // Sample sets (range [j0, j0+count) or list) in `mode`, handling sets too large
 // for a warp and heaps that run out.  The list, if any, is a device array.
 static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, const uint32_t* list,
-                      uint32_t* freq, uint32_t cut, uint32_t qw) {
+                      uint32_t* freq, uint32_t cut, const Shape& sh) {
     hbx_ctx* ctx = p->ctx;
     for (int attempt = 0; count > 0; attempt++) {
         if (attempt > 40) return fail(ctx, HBX_ERR_INTERNAL, "sampling retries did not converge");
         RC(ensure_lists(p, count));
         RC(reset_launch_counters(p));
         const bool timed = mode != MODE_HIST;
-        SampleArgs a = sample_args(p, mode, j0, count, list, freq, cut);
+        SampleArgs a = sample_args(p, mode, j0, count, list, freq, cut, sh);
         if (timed) CK(cudaEventRecord(p->ev0, ctx->stream));
-        CK(launch_sample_warp(a, qw, ctx->sms, ctx->stream));
+        CK(launch_sample_warp(a, sh.qw, ctx->sms, ctx->stream));
         if (timed) CK(cudaEventRecord(p->ev1, ctx->stream));
         p->launches++;
         RC(read_counters(p));
@@ -449,11 +470,17 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
         }
         const uint32_t nbig = (uint32_t)p->hc.big_count;
         if (nbig) {
-            const uint32_t slots = std::min<uint32_t>(nbig, (uint32_t)ctx->sms * 2);
+            // one scratch slot (visited, rank and aux bitmaps + an n-entry queue) per
+            // resident block, at most 8 GB of slots
+            const uint64_t slot_bytes = p->bp_words * 12 + (uint64_t)p->g->n * 4;
+            const uint64_t mem_slots = std::max<uint64_t>(1, (8ull << 30) / slot_bytes);
+            const uint32_t csize = sh.bc ? sh.bc : 1u;
+            uint32_t slots = std::min<uint32_t>(nbig, (uint32_t)block_path_max_clusters(csize));
+            slots = (uint32_t)std::min<uint64_t>(slots, std::max<uint64_t>(mem_slots, p->bp_slots));
             RC(ensure_block_scratch(p, slots));
-            a = sample_args(p, mode, j0, count, list, freq, cut);
+            a = sample_args(p, mode, j0, count, list, freq, cut, sh);
             if (timed) CK(cudaEventRecord(p->ev0, ctx->stream));
-            CK(launch_sample_block(a, nbig, slots, ctx->stream));
+            CK(launch_sample_block(a, nbig, slots, csize, ctx->stream));
             if (timed) CK(cudaEventRecord(p->ev1, ctx->stream));
             p->launches++;
             RC(read_counters(p));
@@ -614,23 +641,27 @@ static int build_codebook(hbx_pool* p, const std::vector<uint32_t>& freq) {
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner: pick the warp capacity QW (the set size above which a set moves
-// from a warp to a whole block) by timing a calibration batch, per graph and
-// model; cached in the context.
+// Autotuner: pick the launch shape of the sampler -- the warp capacity QW (the
+// set size above which a set moves from a warp to a whole block) and the
+// warp's edge-group budget (the scan work above which it does the same) -- by
+// timing a calibration batch per graph and model; cached in the context.
 // ---------------------------------------------------------------------------
-static int choose_qw(hbx_pool* p, uint32_t* qw_out) {
+static int choose_shape(hbx_pool* p, Shape* out) {
     hbx_ctx* ctx = p->ctx;
     if (p->o.warp_capacity) {
-        *qw_out = p->o.warp_capacity;
+        out->qw = p->o.warp_capacity;
+        out->gb = p->o.warp_group_budget ? p->o.warp_group_budget : 2048u;
+        out->bc = p->o.block_cluster ? p->o.block_cluster : 1u;
         return HBX_OK;
     }
-    auto key = std::make_pair((const hbx_graph*)p->g, (int)p->model);
+    auto key = std::make_pair(p->g->fingerprint, (int)p->model);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
-        *qw_out = it->second;
+        *out = it->second;
         return HBX_OK;
     }
-    const uint32_t cands[4] = {128, 256, 512, 1024};
+    const Shape cands[] = {{64, 0, 1},      {128, 256, 1},  {128, 1024, 1}, {256, 4096, 1},
+                           {128, 1024, 2},  {256, 1024, 2}, {256, 4096, 4}, {512, 4096, 1}};
     const uint32_t ncal = 8192;
     uint32_t* freq = nullptr;
     RC(grow_buffer(p, (void**)&freq, 0, (size_t)p->g->n * 4, 0));
@@ -638,13 +669,13 @@ static int choose_qw(hbx_pool* p, uint32_t* qw_out) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    uint32_t best = 256;
+    Shape best = {256, 2048, 1};
     const uint32_t base = 0x40000000u;  // calibration ids, never part of a pool prefix
     const unsigned long long sc0 = p->hc.edges_scanned, lv0 = p->hc.edges_live;
     for (int rep = 0; rep < 2; rep++) {
-        for (uint32_t qw : cands) {
+        for (const Shape& sh : cands) {
             CK(cudaEventRecord(e0, ctx->stream));
-            int r = run_sample(p, MODE_HIST, base, ncal, nullptr, freq, 0u, qw);
+            int r = run_sample(p, MODE_HIST, base, ncal, nullptr, freq, 0u, sh);
             if (r) {
                 dfree(ctx, freq);
                 return r;
@@ -655,7 +686,7 @@ static int choose_qw(hbx_pool* p, uint32_t* qw_out) {
             CK(cudaEventElapsedTime(&ms, e0, e1));
             if (rep == 1 && ms < best_ms) {
                 best_ms = ms;
-                best = qw;
+                best = sh;
             }
         }
     }
@@ -666,7 +697,7 @@ static int choose_qw(hbx_pool* p, uint32_t* qw_out) {
     dfree(ctx, freq);
     p->device_bytes -= (size_t)p->g->n * 4;
     ctx->tuned[key] = best;
-    *qw_out = best;
+    *out = best;
     return HBX_OK;
 }
 
@@ -685,7 +716,7 @@ static int ensure_codebook(hbx_pool* p) {
     const uint32_t n = p->g->n;
     RC(grow_buffer(p, (void**)&freq, 0, (size_t)n * 4, 0));
     const unsigned long long sc0 = p->hc.edges_scanned, lv0 = p->hc.edges_live;
-    int r = run_sample(p, MODE_HIST, 0, (uint32_t)p->W, nullptr, freq, p->o.density_cut, p->qw);
+    int r = run_sample(p, MODE_HIST, 0, (uint32_t)p->W, nullptr, freq, p->o.density_cut, p->shape);
     p->aux_scanned += p->hc.edges_scanned - sc0;
     p->aux_live += p->hc.edges_live - lv0;
     std::vector<uint32_t> hf(n);
@@ -706,7 +737,7 @@ int pool_extend(hbx_pool* p, uint64_t T) {
     if (T >= (1ull << 32)) return fail(ctx, HBX_ERR_INVALID_ARG, "pools hold fewer than 2^32 sets");
     cudaSetDevice(ctx->device);
     const double t0 = now_s();
-    if (!p->qw) RC(choose_qw(p, &p->qw));
+    if (!p->shape.qw) RC(choose_shape(p, &p->shape));
     RC(ensure_codebook(p));
     RC(ensure_recs(p, T));
     const uint32_t mode = p->o.encode ? MODE_ENCODE : MODE_RAW;
@@ -715,7 +746,7 @@ int pool_extend(hbx_pool* p, uint64_t T) {
         const uint64_t j0 = p->T;
         const uint32_t count = (uint32_t)std::min<uint64_t>(T - j0, batch_max);
         const unsigned long long verts_before = p->hc.rr_vertices;
-        RC(run_sample(p, mode, (uint32_t)j0, count, nullptr, nullptr, p->o.density_cut, p->qw));
+        RC(run_sample(p, mode, (uint32_t)j0, count, nullptr, nullptr, p->o.density_cut, p->shape));
         // selection index of the new sets
         const uint64_t added = p->hc.rr_vertices - verts_before;
         const uint64_t items_need = p->hc.chunk_items + added / 32 + 2ull * count + 16;
@@ -740,7 +771,6 @@ int pool_extend(hbx_pool* p, uint64_t T) {
         ia.bm_cap = (uint32_t)std::min<uint64_t>(p->bm_list_cap, 0xFFFFFFFFull);
         ia.ctr = p->ctr;
         ia.moments = p->moments;
-        ia.n = p->g->n;
         CK(launch_index(ia, ctx->stream));
         p->launches++;
         RC(read_counters(p));
@@ -881,6 +911,8 @@ extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint
     if (o.warp_capacity && (o.warp_capacity < 64 || o.warp_capacity > 2048 ||
                             (o.warp_capacity & (o.warp_capacity - 1))))
         return fail(ctx, HBX_ERR_INVALID_ARG, "warp_capacity must be a power of two in [64, 2048]");
+    if (o.block_cluster > 8 || (o.block_cluster & (o.block_cluster - 1)))
+        return fail(ctx, HBX_ERR_INVALID_ARG, "block_cluster must be 0, 1, 2, 4 or 8");
     cudaSetDevice(ctx->device);
     hbx_pool* p = new hbx_pool();
     p->ctx = ctx;
@@ -891,7 +923,7 @@ extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint
     p->W = o.warmup_sets;
     p->bp_words = (((uint64_t)g->n + 31) / 32 + 3) & ~3ull;
     int r = grow_buffer(p, (void**)&p->ctr, 0, sizeof(Counters), 0);
-    if (!r) r = grow_buffer(p, (void**)&p->moments, 0, 4 * sizeof(double), 0);
+    if (!r) r = grow_buffer(p, (void**)&p->moments, 0, 3 * sizeof(double), 0);
     if (!r && (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess))
         r = fail(ctx, HBX_ERR_CUDA, "cudaEventCreate");
     if (!r) {
@@ -987,12 +1019,14 @@ void fill_stats(hbx_pool* p, hbx_stats* s) {
     s->edges_live = p->hc.edges_live - p->aux_live;
     s->code_bits = p->hc.code_bits;
     s->warmup_sets = p->o.encode ? p->W : 0;
-    s->warp_capacity = p->qw;
-    double mom[4] = {0, 0, 0, 0};
-    cudaMemcpyAsync(mom, p->moments, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->ctx->stream);
+    s->warp_capacity = p->shape.qw;
+    s->warp_group_budget = p->shape.gb;
+    s->block_cluster = p->shape.bc;
+    double mom[3] = {0, 0, 0};
+    cudaMemcpyAsync(mom, p->moments, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->ctx->stream);
     cudaStreamSynchronize(p->ctx->stream);
-    // bytes actually held by the sets (heap words in use) plus the 32-byte index
-    s->pool_bytes = (uint64_t)(mom[3] * 4.0) + 32ull * p->T;
+    // bytes held by the sets (heap words written) plus the 16-byte index per set
+    s->pool_bytes = 4ull * p->hc.words_used + sizeof(SetRec) * p->T;
     s->raw_int32_bytes = 4ull * p->hc.rr_vertices + 8ull * p->T;
     if (p->T) {
         const double T = (double)p->T, mean = mom[0] / T;
@@ -1078,6 +1112,54 @@ extern "C" int hbx_imm(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint32_t k, 
 // ===========================================================================
 // inspection
 // ===========================================================================
+namespace hbx {
+// Decode sets [j0, j1) on the device (offsets: host, j1-j0+1 entries already
+// filled; verts: host) and optionally return each Huffman stream's end bit.
+static int decode_range(hbx_pool* p, uint64_t j0, uint64_t j1, const uint64_t* offsets, uint32_t* verts,
+                        uint64_t* ends) {
+    hbx_ctx* ctx = p->ctx;
+    const uint64_t cnt = j1 - j0;
+    unsigned long long* d_off = nullptr;
+    unsigned long long* d_end = nullptr;
+    uint32_t* d_out = nullptr;
+    RC(dalloc(ctx, (void**)&d_off, (cnt + 1) * 8));
+    int r = dalloc(ctx, (void**)&d_out, std::max<uint64_t>(offsets[cnt], 1) * 4);
+    if (!r) r = dalloc(ctx, (void**)&d_end, cnt * 8);
+    if (r) {
+        dfree(ctx, d_off);
+        dfree(ctx, d_out);
+        return r;
+    }
+    DecodeArgs a;
+    a.recs = p->recs;
+    a.raw_heap = p->raw.d;
+    a.code_heap = p->code.d;
+    a.bm_heap = p->bm.d;
+    a.cb = dev_codebook(p);
+    a.has_cb = p->has_cb;
+    a.n = p->g->n;
+    a.j0 = (uint32_t)j0;
+    a.j1 = (uint32_t)j1;
+    a.offsets = d_off;
+    a.out = d_out;
+    a.ends = d_end;
+    a.ctr = p->ctr;
+    cudaError_t e = cudaMemcpyAsync(d_off, offsets, (cnt + 1) * 8, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_end, 0, cnt * 8, ctx->stream);
+    if (e == cudaSuccess) e = launch_decode(a, ctx->stream);
+    p->launches++;
+    if (e == cudaSuccess && offsets[cnt])
+        e = cudaMemcpyAsync(verts, d_out, offsets[cnt] * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && ends) e = cudaMemcpyAsync(ends, d_end, cnt * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, d_off);
+    dfree(ctx, d_out);
+    dfree(ctx, d_end);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "decode");
+    return read_counters(p);
+}
+}  // namespace hbx
+
 extern "C" int hbx_pool_export_set(hbx_pool* p, uint64_t j, uint32_t* kind, uint32_t* size, uint32_t* n_coded,
                                    uint32_t* n_raw, uint64_t* code_bits, uint8_t* payload, uint64_t cap,
                                    uint64_t* nbytes) {
@@ -1088,34 +1170,46 @@ extern "C" int hbx_pool_export_set(hbx_pool* p, uint64_t j, uint32_t* kind, uint
     SetRec r;
     CK(cudaMemcpyAsync(&r, p->recs + j, sizeof(r), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if (kind) *kind = r.kind;
+    const uint32_t k = rec_kind(r);
+    const uint64_t off = rec_off(r);
+    if (k == KIND_PENDING) return fail(ctx, HBX_ERR_INTERNAL, "set not written");
+    uint64_t bits = 0;
+    if (k == KIND_HUFF) {
+        // the stream length is where the decoder stops after n_coded codes
+        std::vector<uint64_t> offs = {0, r.size};
+        std::vector<uint32_t> tmp(std::max<uint32_t>(r.size, 1));
+        RC(decode_range(p, j, j + 1, offs.data(), tmp.data(), &bits));
+    }
+    if (kind) *kind = k;
     if (size) *size = r.size;
-    if (n_coded) *n_coded = r.kind == KIND_HUFF ? r.n_coded : 0;
-    if (n_raw) *n_raw = r.kind == KIND_HUFF ? r.size - r.n_coded : 0;
-    if (code_bits) *code_bits = r.kind == KIND_HUFF ? r.code_bits : 0;
+    if (n_coded) *n_coded = k == KIND_HUFF ? r.n_coded : 0;
+    if (n_raw) *n_raw = k == KIND_HUFF ? r.size - r.n_coded : 0;
+    if (code_bits) *code_bits = bits;
     std::vector<uint8_t> buf;
-    if (r.kind == KIND_HUFF) {
-        const uint32_t nside = r.n_coded ? (r.n_coded - 1) / 32 : 0;
-        const uint64_t cb = (r.code_bits + 7) / 8, cw = (r.code_bits + 31) / 32;
-        const uint64_t raw_at = (cb + 3) & ~3ull;
+    if (k == KIND_HUFF) {
+        const uint32_t nside = side_words(r.n_coded);
         const uint32_t nr = r.size - r.n_coded;
+        const uint64_t cb = (bits + 7) / 8, cw = (bits + 31) / 32;
+        const uint64_t raw_at = (cb + 3) & ~3ull;
         buf.assign(raw_at + 4ull * nr, 0);
         std::vector<uint32_t> words(cw + 1);
-        if (cw) CK(cudaMemcpyAsync(words.data(), p->code.d + r.off + nside, cw * 4, cudaMemcpyDeviceToHost, ctx->stream));
-        if (nr) CK(cudaMemcpyAsync(buf.data() + raw_at, p->raw.d + r.raw_off, 4ull * nr, cudaMemcpyDeviceToHost, ctx->stream));
+        if (cw)
+            CK(cudaMemcpyAsync(words.data(), p->code.d + off + nside + nr, cw * 4, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+        if (nr)
+            CK(cudaMemcpyAsync(buf.data() + raw_at, p->code.d + off + nside, 4ull * nr, cudaMemcpyDeviceToHost,
+                               ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         memcpy(buf.data(), words.data(), cb);
-    } else if (r.kind == KIND_BITMAP) {
+    } else if (k == KIND_BITMAP) {
         const uint64_t nw = ((uint64_t)p->g->n + 31) / 32;
         buf.resize(nw * 4);
-        CK(cudaMemcpyAsync(buf.data(), p->bm.d + r.off, nw * 4, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-    } else if (r.kind == KIND_RAW) {
-        buf.resize(4ull * r.size);
-        CK(cudaMemcpyAsync(buf.data(), p->raw.d + r.off, 4ull * r.size, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(buf.data(), p->bm.d + off, nw * 4, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     } else {
-        return fail(ctx, HBX_ERR_INTERNAL, "set not written");
+        buf.resize(4ull * r.size);
+        CK(cudaMemcpyAsync(buf.data(), p->raw.d + off, 4ull * r.size, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
     }
     if (nbytes) *nbytes = buf.size();
     if (buf.size() > cap || (!payload && buf.size()))
@@ -1132,43 +1226,16 @@ extern "C" int hbx_pool_decode_sets(hbx_pool* p, uint64_t j0, uint64_t j1, uint6
     cudaSetDevice(ctx->device);
     const uint64_t cnt = j1 - j0;
     std::vector<SetRec> recs(cnt);
-    if (cnt) CK(cudaMemcpyAsync(recs.data(), p->recs + j0, cnt * sizeof(SetRec), cudaMemcpyDeviceToHost, ctx->stream));
+    if (cnt)
+        CK(cudaMemcpyAsync(recs.data(), p->recs + j0, cnt * sizeof(SetRec), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     offsets[0] = 0;
     for (uint64_t i = 0; i < cnt; i++) offsets[i + 1] = offsets[i] + recs[i].size;
     if (needed) *needed = offsets[cnt];
-    if (offsets[cnt] > cap || (!verts && offsets[cnt])) return fail(ctx, HBX_ERR_INVALID_ARG, "verts buffer too small");
+    if (offsets[cnt] > cap || (!verts && offsets[cnt]))
+        return fail(ctx, HBX_ERR_INVALID_ARG, "verts buffer too small");
     if (!cnt) return HBX_OK;
-    unsigned long long* d_off = nullptr;
-    uint32_t* d_out = nullptr;
-    RC(dalloc(ctx, (void**)&d_off, (cnt + 1) * 8));
-    int r = dalloc(ctx, (void**)&d_out, std::max<uint64_t>(offsets[cnt], 1) * 4);
-    if (r) {
-        dfree(ctx, d_off);
-        return r;
-    }
-    DecodeArgs a;
-    a.recs = p->recs;
-    a.raw_heap = p->raw.d;
-    a.code_heap = p->code.d;
-    a.bm_heap = p->bm.d;
-    a.cb = dev_codebook(p);
-    a.has_cb = p->has_cb;
-    a.n = p->g->n;
-    a.j0 = (uint32_t)j0;
-    a.j1 = (uint32_t)j1;
-    a.offsets = d_off;
-    a.out = d_out;
-    a.ctr = p->ctr;
-    cudaError_t e = cudaMemcpyAsync(d_off, offsets, (cnt + 1) * 8, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = launch_decode(a, ctx->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(verts, d_out, offsets[cnt] * 4, cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    dfree(ctx, d_off);
-    dfree(ctx, d_out);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "decode");
-    RC(read_counters(p));
+    RC(decode_range(p, j0, j1, offsets, verts, nullptr));
     for (uint64_t i = 0; i < cnt; i++) std::sort(verts + offsets[i], verts + offsets[i + 1]);
     return HBX_OK;
 }

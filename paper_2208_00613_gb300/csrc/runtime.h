@@ -16,6 +16,19 @@
 #include "hbx.h"
 #include "internal.h"
 
+namespace hbx {
+// launch shape of the sampler: warp capacity and warp edge-group budget
+struct Shape {
+    uint32_t qw;
+    uint32_t gb;
+    uint32_t bc;  // blocks per cluster working on one heavy set
+};
+struct Heap {
+    uint32_t* d = nullptr;
+    uint64_t cap = 0;  // words usable (the allocation has slack words beyond)
+};
+}  // namespace hbx
+
 struct hbx_ctx {
     int device = 0;
     int sms = 1;
@@ -30,7 +43,8 @@ struct hbx_ctx {
     std::set<hbx_graph*> graphs;
     std::set<hbx_pool*> pools;
     std::set<hbx_server*> servers;
-    std::map<std::pair<const hbx_graph*, int>, uint32_t> tuned;  // autotuned warp capacity
+    // autotuned launch shapes, keyed by (graph fingerprint, model)
+    std::map<std::pair<uint64_t, int>, hbx::Shape> tuned;
     std::mutex mu;  // guards allocation bookkeeping when a server worker runs
 };
 
@@ -38,18 +52,13 @@ struct hbx_graph {
     hbx_ctx* ctx = nullptr;
     uint32_t n = 0, m = 0;
     uint32_t max_indeg = 0;
+    uint64_t fingerprint = 0;  // hash of sizes and sampled CSR entries
     uint32_t* row_ptr = nullptr;
     uint32_t* col = nullptr;
     float* prob = nullptr;  // 4*ceil(m/4) floats
     uint32_t* q = nullptr;  // LT fixed-point weights
 };
 
-namespace hbx {
-struct Heap {
-    uint32_t* d = nullptr;
-    uint64_t cap = 0;  // words usable (the allocation has slack words beyond)
-};
-}  // namespace hbx
 
 struct hbx_pool {
     hbx_ctx* ctx = nullptr;
@@ -58,7 +67,7 @@ struct hbx_pool {
     uint64_t seed = 0;
     hbx_options o{};
     uint64_t T = 0;
-    uint32_t qw = 0;
+    hbx::Shape shape{0, 0};
     size_t device_bytes = 0;
     hbx::SetRec* recs = nullptr;
     uint64_t rec_cap = 0;

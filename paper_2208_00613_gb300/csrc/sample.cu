@@ -6,7 +6,8 @@
 // in which the search meets its edges:
 //   root   = floor(x * n / 2^32),  x = word 0 of Philox(0, j, epoch, 3)
 //   IC     in-edge e is live iff (x >> 8) * 2^-24 < p[e] (exact fp32), x = word
-//          e%4 of Philox(e/4, j, epoch, 1): one draw serves 4 consecutive edges
+//          e%4 of Philox(e/4, j, epoch, 1): one draw serves the 4 edges of an
+//          aligned group, and a thread handles one group (one float4 of p)
 //   LT     at vertex v, x = word 0 of Philox(v, j, epoch, 2); the walk moves to
 //          the source of the first in-edge whose inclusive prefix sum of fixed-
 //          point weights exceeds x, and stops when there is none or that source
@@ -14,26 +15,38 @@
 //
 // Two kernels:
 //   sample_warp_kernel   one warp per set.  The set's vertex list (the BFS queue)
-//                        and a hash set of visited ids live in shared memory; a
-//                        set that outgrows the warp's capacity QW is handed to
-//                        the block kernel.  The finished set is encoded by the
-//                        same warp: a bitmap if cut*|R| > n, else its vertices
-//                        are mapped to codebook ranks, sorted (bitonic), and the
-//                        codes bit-packed over a prefix sum of code lengths.
-//   sample_block_kernel  one 512-thread block per large set, level-synchronous
-//                        BFS with the visited set as an n-bit bitmap and the
-//                        queue in HBM; the visited bitmap is the bitmap
-//                        encoding, and a rank bitmap gives the sorted code order.
+//                        and a hash set of visited ids live in shared memory.  A
+//                        set that outgrows the warp's capacity QW, or whose
+//                        frontier would exceed the warp's edge-group budget, is
+//                        handed to the block kernel.  The finished set is encoded
+//                        by the same warp: a bitmap if cut*|R| > n, else its
+//                        vertices are mapped to codebook ranks, sorted (bitonic),
+//                        and the codes bit-packed over a prefix sum of lengths.
+//   sample_block_kernel  one thread-block cluster (1 to 8 blocks of 512 threads)
+//                        per heavy set: level-synchronous BFS whose edge groups
+//                        are spread over all blocks of the cluster (a block-wide
+//                        scan of group counts per 512 frontier vertices), level
+//                        barriers on the cluster barrier, the queue tail in block
+//                        0's shared memory (reached by the others through
+//                        distributed shared memory), the visited set as an n-bit
+//                        bitmap and the queue in HBM.  The visited bitmap is the
+//                        bitmap encoding; small Huffman sets are sorted in shared
+//                        memory, large ones through a rank bitmap.
 #include <cstdio>
+
+#include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace hbx {
 
 constexpr int WP_WARPS = 8;
 constexpr int BP_THREADS = 512;
 constexpr int BP_WARPS = BP_THREADS / 32;
+constexpr int BP_ILP = 4;  // edge groups per thread per step of the block path
 constexpr uint32_t WORK_CHUNK = 4;  // sets taken per work-stealing step
 
 struct WarpLocal {
@@ -44,9 +57,7 @@ struct WarpLocal {
     uint32_t stage[40];
 };
 
-__device__ __forceinline__ void set_error(Counters* c, unsigned long long code) {
-    atomicMax(&c->error, code);
-}
+__device__ __forceinline__ void set_error(Counters* c, unsigned long long code) { atomicMax(&c->error, code); }
 
 // Open-addressing insert into a warp's shared hash set (key v+1, 0 = empty).
 // The table holds at most QW + 31 keys in 2*QW slots, so a probe always ends.
@@ -64,8 +75,20 @@ __device__ __forceinline__ bool hash_insert(uint32_t* h, uint32_t mask, uint32_t
     return false;
 }
 
-__device__ __forceinline__ bool ic_live(uint32_t x, float p) {
-    return (float)(x >> 8) * 0x1p-24f < p;
+__device__ __forceinline__ bool ic_live(uint32_t x, float p) { return (float)(x >> 8) * 0x1p-24f < p; }
+
+// Coins of one aligned 4-edge group gg of set j, restricted to [eb, ee).
+// Returns the live mask; adds the in-range edge count to *scanned.
+__device__ __forceinline__ uint32_t group_coins(const SampleArgs& a, uint32_t j, uint32_t gg, uint32_t eb,
+                                                uint32_t ee, unsigned long long* scanned) {
+    const float4 p4 = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
+    const uint4 x = philox4x32_10(make_uint4(gg, j, a.epoch, STREAM_IC), a.key0, a.key1);
+    const uint32_t e0 = gg * 4u;
+    const bool v0 = e0 >= eb && e0 < ee, v1 = e0 + 1 >= eb && e0 + 1 < ee;
+    const bool v2 = e0 + 2 >= eb && e0 + 2 < ee, v3 = e0 + 3 >= eb && e0 + 3 < ee;
+    *scanned += (uint32_t)v0 + (uint32_t)v1 + (uint32_t)v2 + (uint32_t)v3;
+    return (uint32_t)(v0 && ic_live(x.x, p4.x)) | ((uint32_t)(v1 && ic_live(x.y, p4.y)) << 1) |
+           ((uint32_t)(v2 && ic_live(x.z, p4.z)) << 2) | ((uint32_t)(v3 && ic_live(x.w, p4.w)) << 3);
 }
 
 // Bitonic sort of 32 keys held one per lane (ascending by lane).
@@ -78,9 +101,7 @@ __device__ __forceinline__ uint32_t warp_sort32(uint32_t key) {
             const uint32_t other = __shfl_xor_sync(0xFFFFFFFFu, key, jj);
             const bool up = (lane & k) == 0;
             const bool lower = (lane & jj) == 0;
-            // lower partner keeps min when sorting up, max when sorting down
-            const bool keep_min = (lower == up);
-            key = keep_min ? min(key, other) : max(key, other);
+            key = (lower == up) ? min(key, other) : max(key, other);
         }
     }
     return key;
@@ -111,10 +132,11 @@ __device__ void warp_sort_smem(uint32_t* s, uint32_t P) {
 // Warp path
 // ---------------------------------------------------------------------------
 struct WarpStats {
-    unsigned long long scanned = 0, live = 0, verts = 0, bits = 0, huff = 0, bm = 0, raw = 0;
+    unsigned long long scanned = 0, live = 0, verts = 0, bits = 0, huff = 0, bm = 0, raw = 0, words = 0;
 };
 
-// Samples set j into queue[0..tail).  Returns false if it outgrew QW.
+// Samples set j into queue[0..tail).  Returns false if it outgrew QW or the
+// group budget (then the block kernel takes it).
 template <uint32_t QW>
 __device__ bool warp_sample(const SampleArgs& a, uint32_t j, uint32_t* queue, uint32_t* hash, WarpLocal& wl,
                             uint32_t& tail_out, WarpStats& st) {
@@ -132,7 +154,7 @@ __device__ bool warp_sample(const SampleArgs& a, uint32_t j, uint32_t* queue, ui
     bool overflow = false;
 
     if (a.model == MODEL_IC) {
-        uint32_t head = 0;
+        uint32_t head = 0, groups_done = 0;
         while (head < tail && !overflow) {
             const uint32_t cnt = min(32u, tail - head);
             uint32_t b = 0, e = 0, ng = 0, gfirst = 0;
@@ -147,6 +169,11 @@ __device__ bool warp_sample(const SampleArgs& a, uint32_t j, uint32_t* queue, ui
             }
             const uint32_t incl = warp_incl_scan(ng);
             const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            groups_done += total;
+            if (groups_done > a.group_budget) {
+                overflow = true;
+                break;
+            }
             wl.scan[lane] = incl;
             wl.g0[lane] = gfirst;
             wl.eb[lane] = b;
@@ -165,16 +192,7 @@ __device__ bool warp_sample(const SampleArgs& a, uint32_t j, uint32_t* queue, ui
                     }
                     const uint32_t prev = lo ? wl.scan[lo - 1] : 0u;
                     gg = wl.g0[lo] + (t - prev);
-                    const uint32_t eb = wl.eb[lo], ee = wl.ee[lo];
-                    const float4 p4 = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
-                    const uint4 x = philox4x32_10(make_uint4(gg, j, a.epoch, STREAM_IC), a.key0, a.key1);
-                    const uint32_t e0 = gg * 4u;
-                    const bool v0 = e0 >= eb && e0 < ee, v1 = e0 + 1 >= eb && e0 + 1 < ee;
-                    const bool v2 = e0 + 2 >= eb && e0 + 2 < ee, v3 = e0 + 3 >= eb && e0 + 3 < ee;
-                    st.scanned += (uint32_t)v0 + (uint32_t)v1 + (uint32_t)v2 + (uint32_t)v3;
-                    live_mask = (uint32_t)(v0 && ic_live(x.x, p4.x)) | ((uint32_t)(v1 && ic_live(x.y, p4.y)) << 1) |
-                                ((uint32_t)(v2 && ic_live(x.z, p4.z)) << 2) |
-                                ((uint32_t)(v3 && ic_live(x.w, p4.w)) << 3);
+                    live_mask = group_coins(a, j, gg, wl.eb[lo], wl.ee[lo], &st.scanned);
                     st.live += __popc(live_mask);
                 }
                 uint32_t u[4];
@@ -239,6 +257,84 @@ __device__ bool warp_sample(const SampleArgs& a, uint32_t j, uint32_t* queue, ui
     return !overflow;
 }
 
+// Store a Huffman set whose keys (rank, or RAW_FLAG|id for the copy array) are
+// sorted ascending in keys[0..size): allocate its region, pack the codes 32 at a
+// time through `stage` (40 words of shared memory), write the copy array and
+// the record.  Called by one whole warp.  Returns false if the code heap is
+// full (nothing of the set is written).
+__device__ bool warp_huff_store(const SampleArgs& a, uint32_t j, const uint32_t* keys, uint32_t size, uint32_t* stage,
+                                WarpStats& st) {
+    const uint32_t lane = lane_id();
+    uint32_t n_coded = 0, bits = 0;
+    for (uint32_t base = 0; base < size; base += 32) {
+        const uint32_t i = base + lane;
+        const uint32_t key = i < size ? keys[i] : 0xFFFFFFFFu;
+        const bool coded = key < RAW_FLAG;
+        n_coded += __popc(__ballot_sync(0xFFFFFFFFu, coded));
+        bits += warp_sum(coded ? (uint32_t)__ldg(a.cb.len_of_rank + key) : 0u);
+    }
+    const uint32_t n_raw = size - n_coded;
+    const uint32_t nside = side_words(n_coded);
+    const unsigned long long words = (unsigned long long)nside + n_raw + (bits + 31) / 32;
+    unsigned long long off = 0;
+    if (lane == 0) off = words ? atomicAdd(&a.ctr->code_cursor, words) : 0ull;
+    off = __shfl_sync(0xFFFFFFFFu, off, 0);
+    if (off + words > a.code_cap) return false;
+
+    // pack 32 codes at a time into the stage, write completed words
+    uint32_t* out = a.code_heap + off + nside + n_raw;
+    uint32_t carry = 0;  // bit offset of the current chunk's first code
+    for (uint32_t i = lane; i < 40; i += 32) stage[i] = 0;
+    __syncwarp();
+    for (uint32_t c = 0; c * 32 < n_coded; c++) {
+        const uint32_t i = c * 32 + lane;
+        uint32_t L = 0, code = 0;
+        if (i < n_coded) {
+            const uint32_t r = keys[i];
+            L = __ldg(a.cb.len_of_rank + r);
+            code = __ldg(a.cb.code_of_rank + r);
+        }
+        const uint32_t incl = warp_incl_scan(L);
+        const uint32_t chunk_bits = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (c > 0 && lane == 0) a.code_heap[off + c - 1] = carry;
+        const uint32_t wbase = carry >> 5;
+        const uint32_t lo = (carry & 31u) + incl - L;  // offset within the stage
+        if (L) {
+            const uint32_t w = lo >> 5, sh = lo & 31u;
+            if (sh + L <= 32) {
+                atomicOr(&stage[w], code << (32 - sh - L));
+            } else {
+                atomicOr(&stage[w], code >> (sh + L - 32));
+                atomicOr(&stage[w + 1], code << (64 - sh - L));
+            }
+        }
+        __syncwarp();
+        const uint32_t end = carry + chunk_bits;
+        const uint32_t done = (end >> 5) - wbase;  // complete words in the stage
+        for (uint32_t w = lane; w < done; w += 32) out[wbase + w] = bswap32(stage[w]);
+        __syncwarp();
+        const uint32_t partial = stage[done];
+        __syncwarp();
+        for (uint32_t w = lane; w < 40; w += 32) stage[w] = 0;
+        __syncwarp();
+        if (lane == 0) stage[0] = partial;
+        __syncwarp();
+        carry = end;
+    }
+    if ((carry & 31u) && lane == 0) out[carry >> 5] = bswap32(stage[0]);
+    for (uint32_t i = lane; i < n_raw; i += 32) a.code_heap[off + nside + i] = keys[n_coded + i] & ~RAW_FLAG;
+    if (lane == 0) {
+        a.recs[j] = make_rec(KIND_HUFF, off, size, n_coded);
+        st.verts += size;
+        st.bits += bits;
+        st.huff += 1;
+        st.words += words;
+    }
+    __syncwarp();
+    return true;
+}
+
+
 // Encode a finished set held in queue[0..size) and write its record.
 // Returns false if a heap ran out of space (nothing of the set is written).
 template <uint32_t QW>
@@ -258,12 +354,11 @@ __device__ bool warp_emit(const SampleArgs& a, uint32_t j, uint32_t* queue, uint
         if (off + size > a.raw_cap) return false;
         for (uint32_t i = lane; i < size; i += 32) a.raw_heap[off + i] = queue[i];
         if (lane == 0) {
-            SetRec r;
-            r.size = size; r.n_coded = 0; r.code_bits = 0; r.kind = KIND_RAW; r.off = off; r.raw_off = 0;
-            a.recs[j] = r;
+            a.recs[j] = make_rec(KIND_RAW, off, size, 0);
+            st.verts += size;
+            st.raw += 1;
+            st.words += size;
         }
-        st.verts += size * (lane == 0);
-        st.raw += (lane == 0);
         return true;
     }
     // MODE_ENCODE
@@ -278,12 +373,11 @@ __device__ bool warp_emit(const SampleArgs& a, uint32_t j, uint32_t* queue, uint
             atomicOr(&a.bm_heap[off + (v >> 5)], 1u << (v & 31));
         }
         if (lane == 0) {
-            SetRec r;
-            r.size = size; r.n_coded = 0; r.code_bits = 0; r.kind = KIND_BITMAP; r.off = off; r.raw_off = 0;
-            a.recs[j] = r;
+            a.recs[j] = make_rec(KIND_BITMAP, off, size, 0);
+            st.verts += size;
+            st.bm += 1;
+            st.words += row;
         }
-        st.verts += size * (lane == 0);
-        st.bm += (lane == 0);
         return true;
     }
     // Huffman: keys = rank (coded) or RAW_FLAG|id (copy array), sorted ascending
@@ -305,78 +399,7 @@ __device__ bool warp_emit(const SampleArgs& a, uint32_t j, uint32_t* queue, uint
         warp_sort_smem(queue, P);
     }
     __syncwarp();
-    uint32_t n_coded = 0, bits = 0;
-    for (uint32_t base = 0; base < size; base += 32) {
-        const uint32_t i = base + lane;
-        const uint32_t key = i < size ? queue[i] : 0xFFFFFFFFu;
-        const bool coded = key < RAW_FLAG;
-        n_coded += __popc(__ballot_sync(0xFFFFFFFFu, coded));
-        bits += warp_sum(coded ? (uint32_t)__ldg(a.cb.len_of_rank + key) : 0u);
-    }
-    const uint32_t n_raw = size - n_coded;
-    const uint32_t nside = n_coded ? (n_coded - 1) / 32 : 0;
-    const unsigned long long words = nside + (bits + 31) / 32;
-    unsigned long long off = 0, roff = 0;
-    if (lane == 0) {
-        off = words ? atomicAdd(&a.ctr->code_cursor, words) : 0ull;
-        roff = n_raw ? atomicAdd(&a.ctr->raw_cursor, (unsigned long long)n_raw) : 0ull;
-    }
-    off = __shfl_sync(0xFFFFFFFFu, off, 0);
-    roff = __shfl_sync(0xFFFFFFFFu, roff, 0);
-    if (off + words > a.code_cap || roff + n_raw > a.raw_cap) return false;
-
-    // pack 32 codes at a time into the stage, write completed words
-    uint32_t* out = a.code_heap + off + nside;
-    uint32_t carry = 0;  // bit offset of the current chunk's first code
-    for (uint32_t i = lane; i < 40; i += 32) wl.stage[i] = 0;
-    __syncwarp();
-    for (uint32_t c = 0; c * 32 < n_coded; c++) {
-        const uint32_t i = c * 32 + lane;
-        uint32_t L = 0, code = 0;
-        if (i < n_coded) {
-            const uint32_t r = queue[i];
-            L = __ldg(a.cb.len_of_rank + r);
-            code = __ldg(a.cb.code_of_rank + r);
-        }
-        const uint32_t incl = warp_incl_scan(L);
-        const uint32_t chunk_bits = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (c > 0 && lane == 0) a.code_heap[off + c - 1] = carry;
-        const uint32_t wbase = carry >> 5;
-        const uint32_t lo = (carry & 31u) + incl - L;  // offset within the stage
-        if (L) {
-            const uint32_t w = lo >> 5, sh = lo & 31u;
-            if (sh + L <= 32) {
-                atomicOr(&wl.stage[w], code << (32 - sh - L));
-            } else {
-                atomicOr(&wl.stage[w], code >> (sh + L - 32));
-                atomicOr(&wl.stage[w + 1], code << (64 - sh - L));
-            }
-        }
-        __syncwarp();
-        const uint32_t end = carry + chunk_bits;
-        const uint32_t done = (end >> 5) - wbase;  // complete words in the stage
-        for (uint32_t w = lane; w < done; w += 32) out[wbase + w] = bswap32(wl.stage[w]);
-        __syncwarp();
-        const uint32_t partial = wl.stage[done];
-        __syncwarp();
-        for (uint32_t w = lane; w < 40; w += 32) wl.stage[w] = 0;
-        __syncwarp();
-        if (lane == 0) wl.stage[0] = partial;
-        __syncwarp();
-        carry = end;
-    }
-    if ((carry & 31u) && lane == 0) out[carry >> 5] = bswap32(wl.stage[0]);
-    for (uint32_t i = lane; i < n_raw; i += 32) a.raw_heap[roff + i] = queue[n_coded + i] & ~RAW_FLAG;
-    if (lane == 0) {
-        SetRec r;
-        r.size = size; r.n_coded = n_coded; r.code_bits = bits; r.kind = KIND_HUFF; r.off = off; r.raw_off = roff;
-        a.recs[j] = r;
-    }
-    __syncwarp();
-    st.verts += size * (lane == 0);
-    st.bits += bits * (lane == 0);
-    st.huff += (lane == 0);
-    return true;
+    return warp_huff_store(a, j, queue, size, wl.stage, st);
 }
 
 template <uint32_t QW>
@@ -424,9 +447,7 @@ __global__ void __launch_bounds__(WP_WARPS * 32) sample_warp_kernel(SampleArgs a
             reinterpret_cast<uint4*>(hash)[i] = make_uint4(0, 0, 0, 0);
         __syncwarp();
     }
-    // per-warp statistics
-    const unsigned long long s0 = st.scanned, s1 = st.live;
-    unsigned long long sc = s0, lv = s1;
+    unsigned long long sc = st.scanned, lv = st.live;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         sc += __shfl_xor_sync(0xFFFFFFFFu, sc, d);
@@ -440,6 +461,7 @@ __global__ void __launch_bounds__(WP_WARPS * 32) sample_warp_kernel(SampleArgs a
         if (st.huff) atomicAdd(&a.ctr->sets_huff, st.huff);
         if (st.bm) atomicAdd(&a.ctr->sets_bm, st.bm);
         if (st.raw) atomicAdd(&a.ctr->sets_raw, st.raw);
+        if (st.words) atomicAdd(&a.ctr->words_used, st.words);
     }
 }
 
@@ -471,10 +493,9 @@ __device__ uint32_t block_sum(uint32_t v, uint32_t* s_warp) {
     return total;
 }
 
-// Write the set bits of words [0, nwords) in ascending order to out[base..),
+// Write the set bits of words [0, nwords) in ascending order to out[0..),
 // zeroing the words; returns the count.  Each thread takes a contiguous range.
-__device__ uint32_t compact_bits(uint32_t* words, uint64_t nwords, uint32_t* out, uint32_t xor_flag,
-                                 uint32_t* s_warp) {
+__device__ uint32_t compact_bits(uint32_t* words, uint64_t nwords, uint32_t* out, uint32_t* s_warp) {
     const uint64_t per = (nwords + blockDim.x - 1) / blockDim.x;
     const uint64_t w0 = min((uint64_t)threadIdx.x * per, nwords), w1 = min(w0 + per, nwords);
     uint32_t c = 0;
@@ -487,7 +508,7 @@ __device__ uint32_t compact_bits(uint32_t* words, uint64_t nwords, uint32_t* out
         words[w] = 0;
         while (x) {
             const uint32_t b = __ffs(x) - 1;
-            out[pos++] = ((uint32_t)(w * 32) + b) | xor_flag;
+            out[pos++] = (uint32_t)(w * 32) + b;
             x &= x - 1;
         }
     }
@@ -495,207 +516,300 @@ __device__ uint32_t compact_bits(uint32_t* words, uint64_t nwords, uint32_t* out
     return total;
 }
 
+constexpr uint32_t BP_SORT_MAX = 4096;  // sets up to this size are sorted in shared memory
+
+struct BlockShared {
+    uint32_t keys[BP_SORT_MAX];
+    uint32_t stage[40];
+    uint32_t scan[BP_THREADS];
+    uint32_t g0[BP_THREADS];
+    uint32_t eb[BP_THREADS];
+    uint32_t ee[BP_THREADS];
+    uint32_t warp[33];
+    uint32_t tail, item;
+    unsigned long long off;
+    int fail;
+};
+
+// Level-synchronous BFS of set j whose root is queue[0]; returns the size.
+// Level-synchronous BFS of set j whose root is queue[0], by a cluster of
+// csize blocks: every block scans the same frontier chunk and takes every
+// csize-th slice of its edge groups; new vertices are appended through the
+// tail counter in block 0's shared memory.  Returns the set size.
+__device__ uint32_t block_bfs_ic(const SampleArgs& a, uint32_t j, uint32_t* visited, uint32_t* queue, BlockShared& s,
+                                 uint32_t* tail0, uint32_t crank, uint32_t csize, unsigned long long* scanned,
+                                 unsigned long long* live) {
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    uint32_t head = 0;
+    for (;;) {
+        cl.sync();  // the previous level's appends are complete and visible
+        const uint32_t tail = *tail0;
+        cl.sync();  // every block has read the level's end before anyone appends
+        if (head >= tail) break;
+        for (uint32_t c0 = head; c0 < tail; c0 += BP_THREADS) {
+            const uint32_t cnt = min((uint32_t)BP_THREADS, tail - c0);
+            uint32_t b = 0, e = 0, ng = 0, gfirst = 0;
+            if (tid < cnt) {
+                const uint32_t v = queue[c0 + tid];
+                b = __ldg(a.g.row_ptr + v);
+                e = __ldg(a.g.row_ptr + v + 1);
+                if (e > b) {
+                    gfirst = b >> 2;
+                    ng = ((e - 1) >> 2) - gfirst + 1;
+                }
+            }
+            uint32_t total;
+            const uint32_t ex = block_excl_scan(ng, s.warp, total);
+            s.scan[tid] = ex + ng;
+            s.g0[tid] = gfirst;
+            s.eb[tid] = b;
+            s.ee[tid] = e;
+            __syncthreads();
+            // BP_ILP groups per thread per step: their loads and Philox chains
+            // are independent, so they overlap
+            for (uint32_t base = crank * BP_THREADS * BP_ILP; base < total; base += csize * BP_THREADS * BP_ILP) {
+                uint32_t gg[BP_ILP], eb[BP_ILP], ee[BP_ILP];
+                bool ok[BP_ILP];
+#pragma unroll
+                for (int q = 0; q < BP_ILP; q++) {
+                    const uint32_t t = base + q * BP_THREADS + tid;
+                    ok[q] = t < total;
+                    gg[q] = 0;
+                    eb[q] = 0;
+                    ee[q] = 0;
+                    if (ok[q]) {
+                        uint32_t lo = 0, hi = cnt - 1;
+                        while (lo < hi) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (s.scan[mid] > t) hi = mid;
+                            else lo = mid + 1;
+                        }
+                        const uint32_t prev = lo ? s.scan[lo - 1] : 0u;
+                        gg[q] = s.g0[lo] + (t - prev);
+                        eb[q] = s.eb[lo];
+                        ee[q] = s.ee[lo];
+                    }
+                }
+                uint32_t m = 0;  // bit 4q+k: edge 4*gg[q]+k is live
+#pragma unroll
+                for (int q = 0; q < BP_ILP; q++)
+                    if (ok[q]) m |= group_coins(a, j, gg[q], eb[q], ee[q], scanned) << (4 * q);
+                *live += __popc(m);
+                // insert live edges one per lane per round (rare under most models)
+                uint32_t rounds = __reduce_max_sync(0xFFFFFFFFu, (uint32_t)__popc(m));
+                for (uint32_t r = 0; r < rounds; r++) {
+                    bool isnew = false;
+                    uint32_t u = 0;
+                    if (m) {
+                        const uint32_t b = __ffs(m) - 1;
+                        m &= m - 1;
+                        uint32_t g = gg[0];
+#pragma unroll
+                        for (int q = 1; q < BP_ILP; q++)
+                            if ((b >> 2) == (uint32_t)q) g = gg[q];
+                        u = __ldg(a.g.col + g * 4u + (b & 3u));
+                        const uint32_t bit = 1u << (u & 31);
+                        isnew = !(atomicOr(&visited[u >> 5], bit) & bit);
+                    }
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isnew);
+                    if (bal) {
+                        const uint32_t leader = __ffs(bal) - 1;
+                        uint32_t pos = 0;
+                        if (lane == leader) pos = atomicAdd(tail0, (uint32_t)__popc(bal));
+                        pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+                        if (isnew) queue[pos + __popc(bal & lanemask_lt())] = u;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        head = tail;
+    }
+    return head;
+}
+
+// LT walk of set j by warp 0 of block 0 (the walk is sequential); the size is
+// left in block 0's tail counter.
+__device__ void block_walk_lt(const SampleArgs& a, uint32_t j, uint32_t* visited, uint32_t* queue, BlockShared& s,
+                              unsigned long long* scanned, unsigned long long* live) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        uint32_t v = queue[0], tail = 1;
+        for (;;) {
+            const uint32_t b = __ldg(a.g.row_ptr + v), e = __ldg(a.g.row_ptr + v + 1);
+            if (b == e) break;
+            const uint32_t x = philox4x32_10(make_uint4(v, j, a.epoch, STREAM_LT), a.key0, a.key1).x;
+            unsigned long long Q = 0;
+            uint32_t chosen = NONE;
+            for (uint32_t base = b; base < e; base += 32) {
+                const uint32_t idx = base + lane;
+                const uint32_t qi = idx < e ? __ldg(a.g.q + idx) : 0u;
+                const unsigned long long incl = warp_incl_scan_u64(qi) + Q;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, idx < e && (unsigned long long)x < incl);
+                if (bal) {
+                    chosen = base + __ffs(bal) - 1;
+                    break;
+                }
+                Q = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            }
+            *scanned += (chosen == NONE ? e - b : chosen - b + 1) * (lane == 0);
+            if (chosen == NONE) break;
+            *live += (lane == 0);
+            const uint32_t u = __ldg(a.g.col + chosen);
+            uint32_t isnew = 0;
+            if (lane == 0) {
+                const uint32_t bit = 1u << (u & 31);
+                isnew = !(atomicOr(&visited[u >> 5], bit) & bit);
+            }
+            isnew = __shfl_sync(0xFFFFFFFFu, isnew, 0);
+            if (!isnew) break;
+            if (lane == 0) queue[tail] = u;
+            tail++;
+            v = u;
+        }
+        if (lane == 0) s.tail = tail;
+    }
+    __syncthreads();
+}
+
+// One heavy set per thread-block cluster (a cluster of 1 is a plain block).
+// Block 0 of the cluster owns the set's bookkeeping in its shared memory, and
+// encodes the set once the cluster has finished the search.
 __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, uint32_t nbig) {
-    __shared__ WarpLocal wl_all[BP_WARPS];
-    __shared__ uint32_t s_warp[33];
-    __shared__ uint32_t s_tail, s_item;
-    __shared__ unsigned long long s_off, s_roff;
-    __shared__ int s_fail;
+    __shared__ BlockShared s;
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t crank = cl.block_rank(), csize = cl.num_blocks();
+    const uint32_t slot = blockIdx.x / csize;
+    uint32_t* tail0 = cl.map_shared_rank(&s.tail, 0);
+    uint32_t* item0 = cl.map_shared_rank(&s.item, 0);
+    int* fail0 = cl.map_shared_rank(&s.fail, 0);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t n = a.g.n;
-    uint32_t* visited = a.bp_visited + (uint64_t)blockIdx.x * a.bp_words;
-    uint32_t* rbits = a.bp_rbits + (uint64_t)blockIdx.x * a.bp_words;
-    uint32_t* aux = a.bp_aux + (uint64_t)blockIdx.x * a.bp_words;
-    uint32_t* queue = a.bp_queue + (uint64_t)blockIdx.x * n;
-    WarpLocal& wl = wl_all[warp];
+    uint32_t* visited = a.bp_visited + (uint64_t)slot * a.bp_words;
+    uint32_t* rbits = a.bp_rbits + (uint64_t)slot * a.bp_words;
+    uint32_t* aux = a.bp_aux + (uint64_t)slot * a.bp_words;
+    uint32_t* queue = a.bp_queue + (uint64_t)slot * n;
     unsigned long long scanned = 0, live = 0;  // emitted sets only
 
     for (;;) {
         unsigned long long set_scanned = 0, set_live = 0;
-        if (tid == 0) s_item = (uint32_t)min(atomicAdd(&a.ctr->big_work, 1ull), (unsigned long long)nbig);
-        __syncthreads();
-        const uint32_t item = s_item;
-        __syncthreads();
+        if (crank == 0 && tid == 0) s.item = (uint32_t)min(atomicAdd(&a.ctr->big_work, 1ull), (unsigned long long)nbig);
+        cl.sync();
+        const uint32_t item = *item0;
         if (item >= nbig) break;
         const uint32_t j = a.big_list[item];
-        if (tid == 0) {
+        if (crank == 0 && tid == 0) {
             const uint4 rr = philox4x32_10(make_uint4(0u, j, a.epoch, STREAM_ROOT), a.key0, a.key1);
             const uint32_t root = __umulhi(rr.x, n);
             visited[root >> 5] |= 1u << (root & 31);
             queue[0] = root;
-            s_tail = 1;
+            s.tail = 1;
+            s.fail = 0;
         }
-        __syncthreads();
+        uint32_t size;
         if (a.model == MODEL_IC) {
-            uint32_t head = 0;
-            for (;;) {
-                const uint32_t tail = s_tail;
-                __syncthreads();
-                if (head >= tail) break;
-                for (uint32_t c0 = head + warp * 32; c0 < tail; c0 += BP_WARPS * 32) {
-                    const uint32_t cnt = min(32u, tail - c0);
-                    uint32_t b = 0, e = 0, ng = 0, gfirst = 0;
-                    if (lane < cnt) {
-                        const uint32_t v = queue[c0 + lane];
-                        b = __ldg(a.g.row_ptr + v);
-                        e = __ldg(a.g.row_ptr + v + 1);
-                        if (e > b) {
-                            gfirst = b >> 2;
-                            ng = ((e - 1) >> 2) - gfirst + 1;
-                        }
-                    }
-                    const uint32_t incl = warp_incl_scan(ng);
-                    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                    wl.scan[lane] = incl;
-                    wl.g0[lane] = gfirst;
-                    wl.eb[lane] = b;
-                    wl.ee[lane] = e;
-                    __syncwarp();
-                    for (uint32_t base = 0; base < total; base += 32) {
-                        const uint32_t t = base + lane;
-                        uint32_t live_mask = 0, gg = 0;
-                        if (t < total) {
-                            uint32_t lo = 0, hi = cnt - 1;
-                            while (lo < hi) {
-                                const uint32_t mid = (lo + hi) >> 1;
-                                if (wl.scan[mid] > t) hi = mid;
-                                else lo = mid + 1;
-                            }
-                            const uint32_t prev = lo ? wl.scan[lo - 1] : 0u;
-                            gg = wl.g0[lo] + (t - prev);
-                            const uint32_t eb = wl.eb[lo], ee = wl.ee[lo];
-                            const float4 p4 = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
-                            const uint4 x = philox4x32_10(make_uint4(gg, j, a.epoch, STREAM_IC), a.key0, a.key1);
-                            const uint32_t e0 = gg * 4u;
-                            const bool v0 = e0 >= eb && e0 < ee, v1 = e0 + 1 >= eb && e0 + 1 < ee;
-                            const bool v2 = e0 + 2 >= eb && e0 + 2 < ee, v3 = e0 + 3 >= eb && e0 + 3 < ee;
-                            set_scanned += (uint32_t)v0 + (uint32_t)v1 + (uint32_t)v2 + (uint32_t)v3;
-                            live_mask = (uint32_t)(v0 && ic_live(x.x, p4.x)) |
-                                        ((uint32_t)(v1 && ic_live(x.y, p4.y)) << 1) |
-                                        ((uint32_t)(v2 && ic_live(x.z, p4.z)) << 2) |
-                                        ((uint32_t)(v3 && ic_live(x.w, p4.w)) << 3);
-                            set_live += __popc(live_mask);
-                        }
-                        uint32_t u[4];
-#pragma unroll
-                        for (int k = 0; k < 4; k++)
-                            u[k] = (live_mask >> k & 1u) ? __ldg(a.g.col + gg * 4u + k) : 0u;
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            bool isnew = false;
-                            if (live_mask >> k & 1u) {
-                                const uint32_t bit = 1u << (u[k] & 31);
-                                isnew = !(atomicOr(&visited[u[k] >> 5], bit) & bit);
-                            }
-                            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isnew);
-                            if (bal) {
-                                uint32_t pos = 0;
-                                if (lane == (uint32_t)(__ffs(bal) - 1)) pos = atomicAdd(&s_tail, (uint32_t)__popc(bal));
-                                pos = __shfl_sync(0xFFFFFFFFu, pos, __ffs(bal) - 1);
-                                if (isnew) queue[pos + __popc(bal & lanemask_lt())] = u[k];
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
-                __syncthreads();
-                head = tail;
-            }
+            size = block_bfs_ic(a, j, visited, queue, s, tail0, crank, csize, &set_scanned, &set_live);
         } else {
-            if (warp == 0) {
-                uint32_t v = queue[0], tail = 1;
-                for (;;) {
-                    const uint32_t b = __ldg(a.g.row_ptr + v), e = __ldg(a.g.row_ptr + v + 1);
-                    if (b == e) break;
-                    const uint32_t x = philox4x32_10(make_uint4(v, j, a.epoch, STREAM_LT), a.key0, a.key1).x;
-                    unsigned long long Q = 0;
-                    uint32_t chosen = NONE;
-                    for (uint32_t base = b; base < e; base += 32) {
-                        const uint32_t idx = base + lane;
-                        const uint32_t qi = idx < e ? __ldg(a.g.q + idx) : 0u;
-                        const unsigned long long incl = warp_incl_scan_u64(qi) + Q;
-                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, idx < e && (unsigned long long)x < incl);
-                        if (bal) {
-                            chosen = base + __ffs(bal) - 1;
-                            break;
-                        }
-                        Q = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                    }
-                    set_scanned += (chosen == NONE ? e - b : chosen - b + 1) * (lane == 0);
-                    if (chosen == NONE) break;
-                    set_live += (lane == 0);
-                    const uint32_t u = __ldg(a.g.col + chosen);
-                    uint32_t isnew = 0;
-                    if (lane == 0) {
-                        const uint32_t bit = 1u << (u & 31);
-                        isnew = !(atomicOr(&visited[u >> 5], bit) & bit);
-                    }
-                    isnew = __shfl_sync(0xFFFFFFFFu, isnew, 0);
-                    if (!isnew) break;
-                    if (lane == 0) queue[tail] = u;
-                    tail++;
-                    v = u;
-                }
-                if (lane == 0) s_tail = tail;
-            }
-            __syncthreads();
+            cl.sync();
+            if (crank == 0) block_walk_lt(a, j, visited, queue, s, &set_scanned, &set_live);
+            cl.sync();
+            size = *tail0;
         }
-        const uint32_t size = s_tail;
-        __syncthreads();
-
+        if (crank == 0) {
+            __syncthreads();
         // ---- emit ----
         bool clear_by_list = true;
-        if (tid == 0) s_fail = 0;
-        __syncthreads();
         if (a.mode == MODE_HIST) {
             if ((unsigned long long)a.cut * size <= n)
                 for (uint32_t i = tid; i < size; i += BP_THREADS) atomicAdd(&a.freq[queue[i]], 1u);
         } else if (a.mode == MODE_RAW) {
             if (tid == 0) {
-                s_off = atomicAdd(&a.ctr->raw_cursor, (unsigned long long)size);
-                s_fail = s_off + size > a.raw_cap;
+                s.off = atomicAdd(&a.ctr->raw_cursor, (unsigned long long)size);
+                s.fail = s.off + size > a.raw_cap;
             }
             __syncthreads();
-            if (!s_fail) {
-                for (uint32_t i = tid; i < size; i += BP_THREADS) a.raw_heap[s_off + i] = queue[i];
+            if (!s.fail) {
+                for (uint32_t i = tid; i < size; i += BP_THREADS) a.raw_heap[s.off + i] = queue[i];
                 if (tid == 0) {
-                    SetRec r;
-                    r.size = size; r.n_coded = 0; r.code_bits = 0; r.kind = KIND_RAW; r.off = s_off; r.raw_off = 0;
-                    a.recs[j] = r;
+                    a.recs[j] = make_rec(KIND_RAW, s.off, size, 0);
                     atomicAdd(&a.ctr->sets_raw, 1ull);
                     atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                    atomicAdd(&a.ctr->words_used, (unsigned long long)size);
                 }
-            } else if (tid == 0) {
-                a.retry_list[atomicAdd(&a.ctr->retry_count, 1ull)] = j;
             }
         } else if ((unsigned long long)a.cut * size > n) {
             const uint64_t row = a.bp_words;  // ceil(n/32) rounded up to 4
             if (tid == 0) {
-                s_off = atomicAdd(&a.ctr->bm_cursor, (unsigned long long)row);
-                s_fail = s_off + row > a.bm_cap;
+                s.off = atomicAdd(&a.ctr->bm_cursor, (unsigned long long)row);
+                s.fail = s.off + row > a.bm_cap;
             }
             __syncthreads();
             uint4* vis4 = reinterpret_cast<uint4*>(visited);
-            if (!s_fail) {
-                uint4* dst = reinterpret_cast<uint4*>(a.bm_heap + s_off);
+            if (!s.fail) {
+                uint4* dst = reinterpret_cast<uint4*>(a.bm_heap + s.off);
                 for (uint64_t w = tid; w < row / 4; w += BP_THREADS) {
                     dst[w] = vis4[w];
                     vis4[w] = make_uint4(0, 0, 0, 0);
                 }
                 if (tid == 0) {
-                    SetRec r;
-                    r.size = size; r.n_coded = 0; r.code_bits = 0; r.kind = KIND_BITMAP; r.off = s_off; r.raw_off = 0;
-                    a.recs[j] = r;
+                    a.recs[j] = make_rec(KIND_BITMAP, s.off, size, 0);
                     atomicAdd(&a.ctr->sets_bm, 1ull);
                     atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                    atomicAdd(&a.ctr->words_used, (unsigned long long)row);
                 }
             } else {
                 for (uint64_t w = tid; w < row / 4; w += BP_THREADS) vis4[w] = make_uint4(0, 0, 0, 0);
-                if (tid == 0) a.retry_list[atomicAdd(&a.ctr->retry_count, 1ull)] = j;
             }
             clear_by_list = false;
+        } else if (size <= BP_SORT_MAX) {
+            // Huffman, small set: keys sorted in shared memory, visited cleared by list
+            uint32_t P = 2;
+            while (P < size) P <<= 1;
+            for (uint32_t i = tid; i < P; i += BP_THREADS) {
+                uint32_t key = 0xFFFFFFFFu;
+                if (i < size) {
+                    const uint32_t v = queue[i];
+                    const uint32_t r = __ldg(a.cb.rank_of + v);
+                    key = (r != NONE) ? r : (RAW_FLAG | v);
+                    visited[v >> 5] = 0u;
+                }
+                s.keys[i] = key;
+            }
+            __syncthreads();
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (uint32_t i = tid; i < P; i += BP_THREADS) {
+                        const uint32_t ixj = i ^ jj;
+                        if (ixj > i) {
+                            const uint32_t x = s.keys[i], y = s.keys[ixj];
+                            if ((x > y) == ((i & k) == 0)) {
+                                s.keys[i] = y;
+                                s.keys[ixj] = x;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            if (warp == 0) {
+                WarpStats ws;
+                const bool ok = warp_huff_store(a, j, s.keys, size, s.stage, ws);
+                if (lane == 0) {
+                    s.fail = !ok;
+                    if (ok) {
+                        atomicAdd(&a.ctr->sets_huff, 1ull);
+                        atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                        atomicAdd(&a.ctr->code_bits, ws.bits);
+                        atomicAdd(&a.ctr->words_used, ws.words);
+                    }
+                }
+            }
+            __syncthreads();
+            clear_by_list = false;
         } else {
-            // Huffman: ranks into the rank bitmap, coded ids out of the visited bitmap
+            // Huffman, large set: ranks into the rank bitmap, coded ids out of the
+            // visited bitmap, both read back in order
             uint32_t mine = 0;
             for (uint32_t i = tid; i < size; i += BP_THREADS) {
                 const uint32_t v = queue[i];
@@ -706,17 +820,17 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
                     mine++;
                 }
             }
-            const uint32_t n_coded = block_sum(mine, s_warp);  // includes a barrier
-            const uint32_t got_c = compact_bits(rbits, ((uint64_t)a.cb.nsym + 31) / 32, queue, 0u, s_warp);
-            const uint32_t got_r = compact_bits(visited, ((uint64_t)n + 31) / 32, queue + n_coded, 0u, s_warp);
+            const uint32_t n_coded = block_sum(mine, s.warp);  // includes barriers
+            const uint32_t got_c = compact_bits(rbits, ((uint64_t)a.cb.nsym + 31) / 32, queue, s.warp);
+            const uint32_t got_r = compact_bits(visited, ((uint64_t)n + 31) / 32, queue + n_coded, s.warp);
             if (got_c != n_coded || got_r != size - n_coded) set_error(a.ctr, 2);
             const uint32_t n_raw = size - n_coded;
             const uint32_t nch = (n_coded + 31) / 32;
             for (uint32_t c = warp; c < nch; c += BP_WARPS) {
                 const uint32_t i = c * 32 + lane;
                 const uint32_t L = i < n_coded ? (uint32_t)__ldg(a.cb.len_of_rank + queue[i]) : 0u;
-                const uint32_t s = warp_sum(L);
-                if (lane == 0) aux[c] = s;
+                const uint32_t sum = warp_sum(L);
+                if (lane == 0) aux[c] = sum;
             }
             __syncthreads();
             // exclusive scan of chunk bit counts, in place
@@ -725,22 +839,21 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
                 const uint32_t c = t0 + tid;
                 const uint32_t x = c < nch ? aux[c] : 0u;
                 uint32_t tot;
-                const uint32_t ex = block_excl_scan(x, s_warp, tot);
+                const uint32_t ex = block_excl_scan(x, s.warp, tot);
                 if (c < nch) aux[c] = carry + ex;
                 carry += tot;
             }
             __syncthreads();
             const uint32_t bits = carry;
-            const uint32_t nside = n_coded ? (n_coded - 1) / 32 : 0;
-            const unsigned long long words = nside + (bits + 31) / 32;
+            const uint32_t nside = side_words(n_coded);
+            const unsigned long long words = (unsigned long long)nside + n_raw + (bits + 31) / 32;
             if (tid == 0) {
-                s_off = words ? atomicAdd(&a.ctr->code_cursor, words) : 0ull;
-                s_roff = n_raw ? atomicAdd(&a.ctr->raw_cursor, (unsigned long long)n_raw) : 0ull;
-                s_fail = (s_off + words > a.code_cap) || (s_roff + n_raw > a.raw_cap);
+                s.off = words ? atomicAdd(&a.ctr->code_cursor, words) : 0ull;
+                s.fail = s.off + words > a.code_cap;
             }
             __syncthreads();
-            if (!s_fail) {
-                uint32_t* out = a.code_heap + s_off + nside;
+            if (!s.fail) {
+                uint32_t* out = a.code_heap + s.off + nside + n_raw;
                 for (uint32_t c = warp; c < nch; c += BP_WARPS) {
                     const uint32_t i = c * 32 + lane;
                     uint32_t L = 0, code = 0;
@@ -751,7 +864,7 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
                     }
                     const uint32_t incl = warp_incl_scan(L);
                     const uint32_t o = aux[c] + incl - L;
-                    if (c > 0 && lane == 0) a.code_heap[s_off + c - 1] = aux[c];
+                    if (c > 0 && lane == 0) a.code_heap[s.off + c - 1] = aux[c];
                     if (L) {
                         const uint32_t w = o >> 5, sh = o & 31u;
                         if (sh + L <= 32) {
@@ -762,18 +875,14 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
                         }
                     }
                 }
-                for (uint32_t i = tid; i < n_raw; i += BP_THREADS) a.raw_heap[s_roff + i] = queue[n_coded + i];
+                for (uint32_t i = tid; i < n_raw; i += BP_THREADS) a.code_heap[s.off + nside + i] = queue[n_coded + i];
                 if (tid == 0) {
-                    SetRec r;
-                    r.size = size; r.n_coded = n_coded; r.code_bits = bits; r.kind = KIND_HUFF;
-                    r.off = s_off; r.raw_off = s_roff;
-                    a.recs[j] = r;
+                    a.recs[j] = make_rec(KIND_HUFF, s.off, size, n_coded);
                     atomicAdd(&a.ctr->sets_huff, 1ull);
                     atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
                     atomicAdd(&a.ctr->code_bits, (unsigned long long)bits);
+                    atomicAdd(&a.ctr->words_used, words);
                 }
-            } else if (tid == 0) {
-                a.retry_list[atomicAdd(&a.ctr->retry_count, 1ull)] = j;
             }
             clear_by_list = false;
         }
@@ -781,14 +890,20 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
             __syncthreads();
             for (uint32_t i = tid; i < size; i += BP_THREADS) visited[queue[i] >> 5] = 0u;
         }
-        if (tid == 0 && !s_fail) atomicAdd(&a.ctr->sets_big, 1ull);
-        if (!s_fail) {
+        __syncthreads();
+        }  // block 0 encodes
+        cl.sync();  // the set is encoded and the slot is clean
+        const int failed = *fail0;
+        if (crank == 0 && tid == 0) {
+            if (failed) a.retry_list[atomicAdd(&a.ctr->retry_count, 1ull)] = j;
+            else atomicAdd(&a.ctr->sets_big, 1ull);
+        }
+        if (!failed) {
             scanned += set_scanned;
             live += set_live;
         }
-        __syncthreads();
     }
-    // statistics
+    cl.sync();  // no block leaves while another may still read block 0's shared memory
     unsigned long long sc = scanned, lv = live;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -836,12 +951,42 @@ cudaError_t launch_sample_warp(const SampleArgs& a, uint32_t qw, int sms, cudaSt
     }
 }
 
-cudaError_t launch_sample_block(const SampleArgs& a, uint32_t nbig, uint32_t slots, cudaStream_t s) {
+// `slots` clusters of `csize` blocks each
+cudaError_t launch_sample_block(const SampleArgs& a, uint32_t nbig, uint32_t slots, uint32_t csize, cudaStream_t s) {
     if (nbig == 0 || slots == 0) return cudaSuccess;
-    sample_block_kernel<<<slots, BP_THREADS, 0, s>>>(a, nbig);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(slots * csize, 1, 1);
+    cfg.blockDim = dim3(BP_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sample_block_kernel, a, nbig);
 }
 
-int block_path_threads() { return BP_THREADS; }
+// Clusters of `csize` blocks of the block kernel that fit on the GPU at once.
+int block_path_max_clusters(uint32_t csize) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize, 1, 1);
+    cfg.blockDim = dim3(BP_THREADS, 1, 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void*)sample_block_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
 
 }  // namespace hbx

@@ -16,7 +16,7 @@
 //              decoded in 32-code chunks, bitmaps are summed per vertex with
 //              bit-plane counters (the SUBTRACT + POPCOUNT of Eq. (3));
 //   finalize   record u*, its marginal gain, and mark it chosen.
-// Counts are exact u32 integers (the paper's float table is not needed).
+// Counts are exact integers (the paper's float table is not needed).
 #include "common.cuh"
 #include "internal.h"
 
@@ -24,8 +24,7 @@ namespace hbx {
 
 constexpr int SEL_THREADS = 256;
 constexpr int COUNT_THREADS = 512;
-constexpr uint32_t HOT_MAX = 12288;  // ranks privatised in shared memory (48 KB)
-constexpr uint32_t BM_BATCH = 255;   // bitmap sets per bit-plane flush
+constexpr uint32_t BM_BATCH = 255;  // bitmap sets per bit-plane flush
 
 SelShape sel_shape(int sms) {
     SelShape s;
@@ -34,6 +33,26 @@ SelShape sel_shape(int sms) {
     s.cover_blocks = (uint32_t)sms * 4;
     s.dec_blocks = (uint32_t)sms * 4;
     return s;
+}
+
+// Pointers into a Huffman set's region: side index, copy array, code stream.
+struct HuffView {
+    const uint32_t* side;
+    const uint32_t* raw;
+    const uint32_t* words;
+    uint32_t n_coded, n_raw;
+};
+
+__device__ __forceinline__ HuffView huff_view(const uint32_t* code_heap, const SetRec& rec) {
+    HuffView h;
+    const uint64_t off = rec_off(rec);
+    const uint32_t nside = side_words(rec.n_coded);
+    h.n_coded = rec.n_coded;
+    h.n_raw = rec.size - rec.n_coded;
+    h.side = code_heap + off;
+    h.raw = code_heap + off + nside;
+    h.words = code_heap + off + nside + h.n_raw;
+    return h;
 }
 
 __global__ void sel_init_kernel(SelArgs a) {
@@ -50,8 +69,8 @@ __global__ void sel_init_kernel(SelArgs a) {
 
 // ---------------------------------------------------------------------------
 // Initial count over Huffman chunks: one thread decodes one 32-code chunk (or
-// copies 32 copy-array ids).  Hot ranks go to a shared-memory histogram, the
-// rest to cnt with one atomic per group of lanes hitting the same vertex.
+// reads 32 copy-array ids).  Hot ranks go to a shared-memory histogram, the
+// rest to cnt, with one atomic per group of lanes hitting the same counter.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(COUNT_THREADS) count_huff_kernel(SelArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -73,19 +92,17 @@ __global__ void __launch_bounds__(COUNT_THREADS) count_huff_kernel(SelArgs a) {
             const unsigned long long item = a.chunk_items[t];
             const uint32_t j = (uint32_t)(item >> 32), c = (uint32_t)item;
             if (j < a.T) {
-                const SetRec rec = a.recs[j];
-                const uint32_t nch = (rec.n_coded + 31) / 32;
+                const HuffView h = huff_view(a.code_heap, a.recs[j]);
+                const uint32_t nch = (h.n_coded + 31) / 32;
                 if (c < nch) {
-                    const uint32_t nside = (rec.n_coded - 1) / 32;
-                    words = a.code_heap + rec.off + nside;
-                    pos = c ? a.code_heap[rec.off + c - 1] : 0u;
-                    ncodes = min(32u, rec.n_coded - 32 * c);
+                    words = h.words;
+                    pos = c ? h.side[c - 1] : 0u;
+                    ncodes = min(32u, h.n_coded - 32 * c);
                     is_code = 1;
                 } else {
                     const uint32_t rc = c - nch;
-                    const uint32_t n_raw = rec.size - rec.n_coded;
-                    raw = a.raw_heap + rec.raw_off + 32ull * rc;
-                    ncodes = min(32u, n_raw - 32 * rc);
+                    raw = h.raw + 32ull * rc;
+                    ncodes = min(32u, h.n_raw - 32 * rc);
                 }
             }
         }
@@ -121,9 +138,8 @@ __global__ void __launch_bounds__(COUNT_THREADS) count_huff_kernel(SelArgs a) {
 // each listed set in its batch into 8 bit-planes (a ripple-carry adder per bit
 // position), then adds sign * count to cnt[32w + bit].
 __global__ void bitmap_count_kernel(SelArgs a, const uint32_t* list, const uint32_t* list_len_dev,
-                                    uint32_t list_len_host, int sign, int check_alive) {
+                                    uint32_t list_len_host, int sign) {
     const uint32_t nw = (a.n + 31) / 32;
-    const uint64_t row = (((uint64_t)a.n + 31) / 32 + 3) & ~3ull;
     const uint32_t len = list_len_dev ? *list_len_dev : list_len_host;
     const uint32_t nbatch = (len + BM_BATCH - 1) / BM_BATCH;
     const uint64_t total = (uint64_t)nw * nbatch;
@@ -135,9 +151,7 @@ __global__ void bitmap_count_kernel(SelArgs a, const uint32_t* list, const uint3
         for (uint32_t s = s0; s < s1; s++) {
             const uint32_t j = list[s];
             if (j >= a.T) continue;
-            if (check_alive && !a.alive[j]) continue;
-            const SetRec& rec = a.recs[j];
-            uint32_t c = __ldg(a.bm_heap + rec.off + w);
+            uint32_t c = __ldg(a.bm_heap + rec_off(a.recs[j]) + w);
 #pragma unroll
             for (int i = 0; i < 8; i++) {
                 const uint32_t t2 = p[i] & c;
@@ -145,7 +159,6 @@ __global__ void bitmap_count_kernel(SelArgs a, const uint32_t* list, const uint3
                 c = t2;
             }
         }
-        (void)row;
         const uint32_t any = p[0] | p[1] | p[2] | p[3] | p[4] | p[5] | p[6] | p[7];
         if (!any) continue;
         for (uint32_t bit = 0; bit < 32; bit++) {
@@ -165,7 +178,8 @@ __global__ void count_raw_kernel(SelArgs a) {
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
     for (uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < a.T; j += nwarps) {
         const SetRec rec = a.recs[j];
-        for (uint32_t i = lane; i < rec.size; i += 32) atomicAdd(&a.cnt[a.raw_heap[rec.off + i]], 1);
+        const uint32_t* x = a.raw_heap + rec_off(rec);
+        for (uint32_t i = lane; i < rec.size; i += 32) atomicAdd(&a.cnt[x[i]], 1);
     }
 }
 
@@ -229,24 +243,22 @@ __global__ void __launch_bounds__(SEL_THREADS) argmax_kernel(SelArgs a) {
 
 // Membership of rank ru in a Huffman set: binary search on the first code of
 // each 32-code chunk, then a scan of one chunk, stopping at the first rank >= ru.
-__device__ bool huff_contains(const DecodeSmem& ds, const uint32_t* __restrict__ code_heap, const SetRec& rec,
-                              uint32_t ru) {
-    const uint32_t n = rec.n_coded;
+__device__ bool huff_contains(const DevCodebook& cb, const HuffView& h, uint32_t ru) {
+    const uint32_t n = h.n_coded;
     if (n == 0) return false;
-    const uint32_t nside = (n - 1) / 32;
-    const uint32_t* words = code_heap + rec.off + nside;
+    const uint32_t nside = side_words(n);
     uint32_t lo = 0, hi = nside;
     while (lo < hi) {
         const uint32_t mid = (lo + hi + 1) >> 1;
-        uint64_t pos = __ldg(code_heap + rec.off + mid - 1);
-        const uint32_t r = decode_one(ds, words, pos);
+        uint64_t pos = __ldg(h.side + mid - 1);
+        const uint32_t r = decode_one_g(cb, h.words, pos);
         if (r <= ru) lo = mid;
         else hi = mid - 1;
     }
-    uint64_t pos = lo ? __ldg(code_heap + rec.off + lo - 1) : 0u;
+    uint64_t pos = lo ? __ldg(h.side + lo - 1) : 0u;
     const uint32_t cnt = min(32u, n - 32 * lo);
     for (uint32_t i = 0; i < cnt; i++) {
-        const uint32_t r = decode_one(ds, words, pos);
+        const uint32_t r = decode_one_g(cb, h.words, pos);
         if (r >= ru) return r == ru;
     }
     return false;
@@ -264,29 +276,29 @@ __device__ bool sorted_contains(const uint32_t* __restrict__ x, uint32_t len, ui
 }
 
 __global__ void __launch_bounds__(SEL_THREADS) cover_kernel(SelArgs a) {
-    __shared__ DecodeSmem ds;
-    if (a.has_cb) load_decode_smem(ds, a.cb);
-    __syncthreads();
     const uint32_t u = a.st->u;
     const uint32_t ru = a.has_cb ? __ldg(a.cb.rank_of + u) : NONE;
     unsigned long long gain = 0;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < a.T; j += gridDim.x * blockDim.x) {
         if (!a.alive[j]) continue;
         const SetRec rec = a.recs[j];
+        const uint32_t kind = rec_kind(rec);
         bool member = false;
-        if (rec.kind == KIND_HUFF) {
-            if (ru != NONE) member = huff_contains(ds, a.code_heap, rec, ru);
-            else member = sorted_contains(a.raw_heap + rec.raw_off, rec.size - rec.n_coded, u);
-        } else if (rec.kind == KIND_BITMAP) {
-            member = (__ldg(a.bm_heap + rec.off + (u >> 5)) >> (u & 31)) & 1u;
+        if (kind == KIND_HUFF) {
+            const HuffView h = huff_view(a.code_heap, rec);
+            if (ru != NONE) member = huff_contains(a.cb, h, ru);
+            else member = sorted_contains(h.raw, h.n_raw, u);
+        } else if (kind == KIND_BITMAP) {
+            member = (__ldg(a.bm_heap + rec_off(rec) + (u >> 5)) >> (u & 31)) & 1u;
         } else {
-            for (uint32_t i = 0; i < rec.size && !member; i++) member = __ldg(a.raw_heap + rec.off + i) == u;
+            const uint32_t* x = a.raw_heap + rec_off(rec);
+            for (uint32_t i = 0; i < rec.size && !member; i++) member = __ldg(x + i) == u;
         }
         if (member) {
             a.alive[j] = 0;
             gain++;
-            if (rec.kind == KIND_HUFF) a.cov_huff[atomicAdd(&a.st->n_cov_huff, 1u)] = j;
-            else if (rec.kind == KIND_BITMAP) a.cov_bm[atomicAdd(&a.st->n_cov_bm, 1u)] = j;
+            if (kind == KIND_HUFF) a.cov_huff[atomicAdd(&a.st->n_cov_huff, 1u)] = j;
+            else if (kind == KIND_BITMAP) a.cov_bm[atomicAdd(&a.st->n_cov_bm, 1u)] = j;
             else a.cov_raw[atomicAdd(&a.st->n_cov_raw, 1u)] = j;
         }
     }
@@ -296,28 +308,21 @@ __global__ void __launch_bounds__(SEL_THREADS) cover_kernel(SelArgs a) {
 
 // Covered Huffman sets: one warp per set, lanes over 32-code chunks.
 __global__ void __launch_bounds__(SEL_THREADS) dec_huff_kernel(SelArgs a) {
-    __shared__ DecodeSmem ds;
-    load_decode_smem(ds, a.cb);
-    __syncthreads();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
     const uint32_t len = a.st->n_cov_huff;
     for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += nwarps) {
-        const SetRec rec = a.recs[a.cov_huff[i]];
-        const uint32_t n = rec.n_coded;
-        const uint32_t nch = (n + 31) / 32;
-        const uint32_t nside = n ? (n - 1) / 32 : 0;
-        const uint32_t* words = a.code_heap + rec.off + nside;
+        const HuffView h = huff_view(a.code_heap, a.recs[a.cov_huff[i]]);
+        const uint32_t nch = (h.n_coded + 31) / 32;
         for (uint32_t c = lane; c < nch; c += 32) {
-            uint64_t pos = c ? __ldg(a.code_heap + rec.off + c - 1) : 0u;
-            const uint32_t cnt = min(32u, n - 32 * c);
+            uint64_t pos = c ? __ldg(h.side + c - 1) : 0u;
+            const uint32_t cnt = min(32u, h.n_coded - 32 * c);
             for (uint32_t k = 0; k < cnt; k++) {
-                const uint32_t r = decode_one(ds, words, pos);
+                const uint32_t r = decode_one_g(a.cb, h.words, pos);
                 if (r != NONE) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -1);
             }
         }
-        const uint32_t n_raw = rec.size - n;
-        for (uint32_t k = lane; k < n_raw; k += 32) atomicAdd(&a.cnt[__ldg(a.raw_heap + rec.raw_off + k)], -1);
+        for (uint32_t k = lane; k < h.n_raw; k += 32) atomicAdd(&a.cnt[__ldg(h.raw + k)], -1);
     }
 }
 
@@ -327,7 +332,8 @@ __global__ void __launch_bounds__(SEL_THREADS) dec_raw_kernel(SelArgs a) {
     const uint32_t len = a.st->n_cov_raw;
     for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += nwarps) {
         const SetRec rec = a.recs[a.cov_raw[i]];
-        for (uint32_t k = lane; k < rec.size; k += 32) atomicAdd(&a.cnt[__ldg(a.raw_heap + rec.off + k)], -1);
+        const uint32_t* x = a.raw_heap + rec_off(rec);
+        for (uint32_t k = lane; k < rec.size; k += 32) atomicAdd(&a.cnt[__ldg(x + k)], -1);
     }
 }
 
@@ -369,7 +375,7 @@ cudaError_t launch_count(const SelArgs& a, uint32_t encode, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     if (a.n_bm) {
-        bitmap_count_kernel<<<sh.count_blocks * 2, SEL_THREADS, 0, s>>>(a, a.bm_sets, nullptr, a.n_bm, 1, 0);
+        bitmap_count_kernel<<<sh.count_blocks * 2, SEL_THREADS, 0, s>>>(a, a.bm_sets, nullptr, a.n_bm, 1);
         return cudaGetLastError();
     }
     return cudaSuccess;
@@ -383,12 +389,12 @@ cudaError_t launch_argmax(const SelArgs& a, cudaStream_t s) {
 
 cudaError_t launch_iteration(const SelArgs& a, uint32_t encode, cudaStream_t s) {
     const SelShape sh = sel_shape(a.sms);
+    const uint32_t cover_blocks = min(sh.cover_blocks, (a.T + SEL_THREADS - 1) / SEL_THREADS);
     argmax_kernel<<<sh.argmax_blocks, SEL_THREADS, 0, s>>>(a);
-    cover_kernel<<<sh.cover_blocks, SEL_THREADS, 0, s>>>(a);
+    cover_kernel<<<cover_blocks ? cover_blocks : 1u, SEL_THREADS, 0, s>>>(a);
     if (encode) {
-        if (a.has_cb) dec_huff_kernel<<<sh.dec_blocks, SEL_THREADS, 0, s>>>(a);
-        if (a.n_bm)
-            bitmap_count_kernel<<<sh.dec_blocks, SEL_THREADS, 0, s>>>(a, a.cov_bm, &a.st->n_cov_bm, 0, -1, 0);
+        if (a.has_cb) dec_huff_kernel<<<(uint32_t)a.sms, SEL_THREADS, 0, s>>>(a);
+        if (a.n_bm) bitmap_count_kernel<<<sh.dec_blocks, SEL_THREADS, 0, s>>>(a, a.cov_bm, &a.st->n_cov_bm, 0, -1);
     } else {
         dec_raw_kernel<<<sh.dec_blocks, SEL_THREADS, 0, s>>>(a);
     }
@@ -402,12 +408,12 @@ cudaError_t launch_iteration(const SelArgs& a, uint32_t encode, cudaStream_t s) 
 // Eq. (2).
 // ---------------------------------------------------------------------------
 __global__ void index_kernel(IndexArgs a) {
-    __shared__ double s_m[4][SEL_THREADS / 32];
-    double m1 = 0, m2 = 0, m3 = 0, m4 = 0;
-    const uint64_t row = (((uint64_t)a.n + 31) / 32 + 3) & ~3ull;
+    __shared__ double s_m[3][SEL_THREADS / 32];
+    double m1 = 0, m2 = 0, m3 = 0;
     for (uint32_t j = a.j0 + blockIdx.x * blockDim.x + threadIdx.x; j < a.j1; j += gridDim.x * blockDim.x) {
         const SetRec rec = a.recs[j];
-        if (rec.kind == KIND_PENDING) {
+        const uint32_t kind = rec_kind(rec);
+        if (kind == KIND_PENDING) {
             atomicMax(&a.ctr->error, 3ull);
             continue;
         }
@@ -415,14 +421,7 @@ __global__ void index_kernel(IndexArgs a) {
         m1 += x;
         m2 += x * x;
         m3 += x * x * x;
-        if (rec.kind == KIND_HUFF)
-            m4 += (double)((rec.n_coded ? (rec.n_coded - 1) / 32 : 0) + (rec.code_bits + 31) / 32 +
-                           (rec.size - rec.n_coded));
-        else if (rec.kind == KIND_BITMAP)
-            m4 += (double)row;
-        else
-            m4 += x;
-        if (rec.kind == KIND_HUFF) {
+        if (kind == KIND_HUFF) {
             const uint32_t nch = (rec.n_coded + 31) / 32 + (rec.size - rec.n_coded + 31) / 32;
             const unsigned long long base = atomicAdd(&a.ctr->chunk_items, (unsigned long long)nch);
             if (base + nch > a.items_cap) {
@@ -430,7 +429,7 @@ __global__ void index_kernel(IndexArgs a) {
                 continue;
             }
             for (uint32_t c = 0; c < nch; c++) a.chunk_items[base + c] = ((unsigned long long)j << 32) | c;
-        } else if (rec.kind == KIND_BITMAP) {
+        } else if (kind == KIND_BITMAP) {
             const unsigned long long b = atomicAdd(&a.ctr->bm_list, 1ull);
             if (b >= a.bm_cap) {
                 atomicMax(&a.ctr->error, 4ull);
@@ -444,16 +443,14 @@ __global__ void index_kernel(IndexArgs a) {
         m1 += __shfl_xor_sync(0xFFFFFFFFu, m1, d);
         m2 += __shfl_xor_sync(0xFFFFFFFFu, m2, d);
         m3 += __shfl_xor_sync(0xFFFFFFFFu, m3, d);
-        m4 += __shfl_xor_sync(0xFFFFFFFFu, m4, d);
     }
     if ((threadIdx.x & 31) == 0) {
         s_m[0][threadIdx.x >> 5] = m1;
         s_m[1][threadIdx.x >> 5] = m2;
         s_m[2][threadIdx.x >> 5] = m3;
-        s_m[3][threadIdx.x >> 5] = m4;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < 3) {
         double t = 0;
         for (int i = 0; i < SEL_THREADS / 32; i++) t += s_m[threadIdx.x][i];
         if (t != 0) atomicAdd(&a.moments[threadIdx.x], t);
@@ -471,7 +468,7 @@ cudaError_t launch_index(const IndexArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Decode sets [j0, j1) to vertex lists (one warp per set), for inspection.
 // Huffman: vertices in rank order then the copy array; bitmap: ascending;
-// raw: as stored.
+// raw: as stored.  ends[j - j0] receives the bit position after the last code.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(SEL_THREADS) decode_kernel(DecodeArgs a) {
     __shared__ DecodeSmem ds;
@@ -481,17 +478,16 @@ __global__ void __launch_bounds__(SEL_THREADS) decode_kernel(DecodeArgs a) {
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
     for (uint32_t j = a.j0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < a.j1; j += nwarps) {
         const SetRec rec = a.recs[j];
+        const uint32_t kind = rec_kind(rec);
         uint32_t* out = a.out + a.offsets[j - a.j0];
-        if (rec.kind == KIND_HUFF) {
-            const uint32_t n = rec.n_coded;
-            const uint32_t nch = (n + 31) / 32;
-            const uint32_t nside = n ? (n - 1) / 32 : 0;
-            const uint32_t* words = a.code_heap + rec.off + nside;
+        if (kind == KIND_HUFF) {
+            const HuffView h = huff_view(a.code_heap, rec);
+            const uint32_t nch = (h.n_coded + 31) / 32;
             for (uint32_t c = lane; c < nch; c += 32) {
-                uint64_t pos = c ? a.code_heap[rec.off + c - 1] : 0u;
-                const uint32_t cnt = min(32u, n - 32 * c);
+                uint64_t pos = c ? h.side[c - 1] : 0u;
+                const uint32_t cnt = min(32u, h.n_coded - 32 * c);
                 for (uint32_t k = 0; k < cnt; k++) {
-                    const uint32_t r = decode_one(ds, words, pos);
+                    const uint32_t r = decode_one(ds, h.words, pos);
                     if (r == NONE) {
                         atomicMax(&a.ctr->error, 5ull);
                         out[32 * c + k] = NONE;
@@ -499,15 +495,17 @@ __global__ void __launch_bounds__(SEL_THREADS) decode_kernel(DecodeArgs a) {
                         out[32 * c + k] = a.cb.vertex_of_rank[r];
                     }
                 }
-                if (c == nch - 1 && pos != rec.code_bits) atomicMax(&a.ctr->error, 6ull);
+                if (c == nch - 1 && a.ends) a.ends[j - a.j0] = pos;
             }
-            for (uint32_t k = lane; k < rec.size - n; k += 32) out[n + k] = a.raw_heap[rec.raw_off + k];
-        } else if (rec.kind == KIND_BITMAP) {
+            if (nch == 0 && lane == 0 && a.ends) a.ends[j - a.j0] = 0;
+            for (uint32_t k = lane; k < h.n_raw; k += 32) out[h.n_coded + k] = h.raw[k];
+        } else if (kind == KIND_BITMAP) {
             const uint32_t nw = (a.n + 31) / 32;
+            const uint32_t* row = a.bm_heap + rec_off(rec);
             uint32_t base = 0;
             for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
                 const uint32_t w = w0 + lane;
-                uint32_t x = w < nw ? a.bm_heap[rec.off + w] : 0u;
+                uint32_t x = w < nw ? row[w] : 0u;
                 const uint32_t c = __popc(x);
                 const uint32_t incl = warp_incl_scan(c);
                 uint32_t p = base + incl - c;
@@ -518,8 +516,11 @@ __global__ void __launch_bounds__(SEL_THREADS) decode_kernel(DecodeArgs a) {
                 }
                 base += __shfl_sync(0xFFFFFFFFu, incl, 31);
             }
-        } else {
-            for (uint32_t k = lane; k < rec.size; k += 32) out[k] = a.raw_heap[rec.off + k];
+        } else if (kind == KIND_RAW) {
+            const uint32_t* x = a.raw_heap + rec_off(rec);
+            for (uint32_t k = lane; k < rec.size; k += 32) out[k] = x[k];
+        } else if (lane == 0) {
+            atomicMax(&a.ctr->error, 3ull);
         }
     }
 }
