@@ -276,6 +276,29 @@ int hbx_wait(hbx_ticket *t, uint32_t *seeds_out, double *influence_out, hbx_stat
 int hbx_cancel(hbx_ticket *t);
 void hbx_ticket_destroy(hbx_ticket *t);
 
+/*
+ * Allocation-free argmax over a device array of counts.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory where they need it -- a service that reserves all of its GPU memory up
+ * front and must stay within that fixed budget, or code running inside a
+ * memory allocator's own hook, where allocating again would re-enter the
+ * allocator.  It runs the selection's argmax (largest count, lowest id on
+ * ties; any int32 values) but keeps its scratch (per-block partial maxima and a
+ * finish counter, 32 KB) in a static device array that every device loading
+ * the library holds until the process exits.  It calls no allocation routine.
+ *   d_counts  device pointer, n int32 counts, on the current device.
+ *   n         1 .. HBX_ARGMAX_NOALLOC_MAX; larger n fails with INVALID_ARG.
+ *   d_out     device pointer to one uint32: the winning index, written when the
+ *             stream reaches the launch (the call does not synchronise).
+ *   stream    cudaStream_t of the current device (NULL = legacy default stream).
+ * The first call on a device looks up the scratch array's device address (once
+ * per device, with that device current).  All calls on a device share the
+ * array: calls whose launches overlap on the GPU race and must be ordered by
+ * the caller (one stream, or events).  Errors: INVALID_ARG, CUDA.
+ */
+#define HBX_ARGMAX_NOALLOC_MAX 16777216u
+int hbx_argmax_noalloc(const int32_t *d_counts, uint32_t n, uint32_t *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

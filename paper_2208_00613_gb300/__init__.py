@@ -97,6 +97,7 @@ def lib():
         "hbx_wait": (I, [P, P, P, P, P, I64]),
         "hbx_cancel": (I, [P]),
         "hbx_ticket_destroy": (None, [P]),
+        "hbx_argmax_noalloc": (I, [P, U32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -299,6 +300,13 @@ def hbx_cancel(ticket) -> int:
 
 def hbx_ticket_destroy(ticket):
     lib().hbx_ticket_destroy(ticket)
+
+
+def hbx_argmax_noalloc(d_counts: int, n: int, d_out: int, stream: int | None = None) -> int:
+    """Allocation-free argmax (see include/hbx.h): device pointers in, the
+    winning index written to d_out on `stream`.  Returns the raw code."""
+    return lib().hbx_argmax_noalloc(ctypes.c_void_p(d_counts), n, ctypes.c_void_p(d_out),
+                                    ctypes.c_void_p(stream) if stream else None)
 
 
 # ---------------------------------------------------------------------------
