@@ -27,7 +27,10 @@ using namespace hbx;
 namespace hbx {
 
 int fail(hbx_ctx* c, int code, const std::string& msg) {
-    if (c) c->last_error = msg;
+    if (c) {
+        std::lock_guard<std::mutex> lock(c->mu);
+        c->last_error = msg;
+    }
     return code;
 }
 
@@ -55,17 +58,23 @@ int dalloc(hbx_ctx* c, void** p, size_t bytes) {
             return fail(c, HBX_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
         }
     }
-    c->live_bytes += bytes;
-    c->sizes[*p] = bytes;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        c->live_bytes += bytes;
+        c->sizes[*p] = bytes;
+    }
     return HBX_OK;
 }
 
 void dfree(hbx_ctx* c, void* p) {
     if (!p) return;
-    auto it = c->sizes.find(p);
-    if (it != c->sizes.end()) {
-        c->live_bytes -= it->second;
-        c->sizes.erase(it);
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        auto it = c->sizes.find(p);
+        if (it != c->sizes.end()) {
+            c->live_bytes -= it->second;
+            c->sizes.erase(it);
+        }
     }
     if (c->free_fn) c->free_fn(p, c->alloc_user);
     else cudaFree(p);
@@ -326,10 +335,10 @@ int grow_buffer(hbx_pool* p, void** buf, size_t old_bytes, size_t new_bytes, siz
     RC(pool_bytes_check(p, new_bytes > old_bytes ? new_bytes - old_bytes : 0));
     void* nb = nullptr;
     RC(dalloc(ctx, &nb, new_bytes));
-    CK(cudaMemsetAsync(nb, 0, new_bytes, ctx->stream));
-    if (*buf && keep) CK(cudaMemcpyAsync(nb, *buf, keep, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemsetAsync(nb, 0, new_bytes, p->stream));
+    if (*buf && keep) CK(cudaMemcpyAsync(nb, *buf, keep, cudaMemcpyDeviceToDevice, p->stream));
     if (*buf) {
-        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaStreamSynchronize(p->stream));
         dfree(ctx, *buf);
     }
     *buf = nb;
@@ -360,10 +369,10 @@ static int ensure_recs(hbx_pool* p, uint64_t T) {
     RC(pool_bytes_check(p, (nc - p->rec_cap) * sizeof(SetRec)));
     void* nb = nullptr;
     RC(dalloc(ctx, &nb, nc * sizeof(SetRec)));
-    CK(cudaMemsetAsync(nb, 0xFF, nc * sizeof(SetRec), ctx->stream));
+    CK(cudaMemsetAsync(nb, 0xFF, nc * sizeof(SetRec), p->stream));
     if (b) {
-        CK(cudaMemcpyAsync(nb, b, p->rec_cap * sizeof(SetRec), cudaMemcpyDeviceToDevice, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpyAsync(nb, b, p->rec_cap * sizeof(SetRec), cudaMemcpyDeviceToDevice, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
         dfree(ctx, b);
     }
     p->device_bytes += (nc - p->rec_cap) * sizeof(SetRec);
@@ -396,8 +405,8 @@ static int ensure_block_scratch(hbx_pool* p, uint32_t slots) {
 
 static int read_counters(hbx_pool* p) {
     hbx_ctx* ctx = p->ctx;
-    CK(cudaMemcpyAsync(&p->hc, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(&p->hc, p->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
     if (p->hc.error) return fail(ctx, HBX_ERR_INTERNAL, "kernel error code " + std::to_string(p->hc.error));
     return HBX_OK;
 }
@@ -405,8 +414,8 @@ static int read_counters(hbx_pool* p) {
 // zero the per-launch fields of the device counters
 static int reset_launch_counters(hbx_pool* p) {
     hbx_ctx* ctx = p->ctx;
-    CK(cudaMemsetAsync(p->ctr, 0, 2 * sizeof(unsigned long long), ctx->stream));  // work, big_work
-    CK(cudaMemsetAsync(&p->ctr->big_count, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(p->ctr, 0, 2 * sizeof(unsigned long long), p->stream));  // work, big_work
+    CK(cudaMemsetAsync(&p->ctr->big_count, 0, 2 * sizeof(unsigned long long), p->stream));
     return HBX_OK;
 }
 
@@ -457,9 +466,9 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
         RC(reset_launch_counters(p));
         const bool timed = mode != MODE_HIST;
         SampleArgs a = sample_args(p, mode, j0, count, list, freq, cut, sh);
-        if (timed) CK(cudaEventRecord(p->ev0, ctx->stream));
-        CK(launch_sample_warp(a, sh.qw, ctx->sms, ctx->stream));
-        if (timed) CK(cudaEventRecord(p->ev1, ctx->stream));
+        if (timed) CK(cudaEventRecord(p->ev0, p->stream));
+        CK(launch_sample_warp(a, sh.qw, ctx->sms, p->stream));
+        if (timed) CK(cudaEventRecord(p->ev1, p->stream));
         p->launches++;
         RC(read_counters(p));
         if (timed) {
@@ -479,9 +488,9 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
             slots = (uint32_t)std::min<uint64_t>(slots, std::max<uint64_t>(mem_slots, p->bp_slots));
             RC(ensure_block_scratch(p, slots));
             a = sample_args(p, mode, j0, count, list, freq, cut, sh);
-            if (timed) CK(cudaEventRecord(p->ev0, ctx->stream));
-            CK(launch_sample_block(a, nbig, slots, csize, ctx->stream));
-            if (timed) CK(cudaEventRecord(p->ev1, ctx->stream));
+            if (timed) CK(cudaEventRecord(p->ev0, p->stream));
+            CK(launch_sample_block(a, nbig, slots, csize, p->stream));
+            if (timed) CK(cudaEventRecord(p->ev1, p->stream));
             p->launches++;
             RC(read_counters(p));
             if (timed) {
@@ -498,7 +507,7 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
         RC(grow_heap(p, p->code, p->hc.code_cursor + 1024));
         const uint64_t row = (((uint64_t)p->g->n + 31) / 32 + 3) & ~3ull;
         RC(grow_heap(p, p->bm, p->hc.bm_cursor + (p->hc.bm_cursor > p->bm.cap ? 8 * row : 0)));
-        CK(cudaMemcpyAsync(p->list_in, p->retry_list, (size_t)nretry * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(p->list_in, p->retry_list, (size_t)nretry * 4, cudaMemcpyDeviceToDevice, p->stream));
         list = p->list_in;
         count = nretry;
         j0 = 0;
@@ -626,7 +635,7 @@ static int build_codebook(hbx_pool* p, const std::vector<uint32_t>& freq) {
     p->max_len = maxL;
     auto up = [&](void** dst, const void* src, size_t bytes) -> int {
         RC(grow_buffer(p, dst, 0, bytes + 16, 0));
-        CK(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, p->stream));
         return HBX_OK;
     };
     RC(up((void**)&p->rank_of, rank_of.data(), (size_t)n * 4));
@@ -635,7 +644,7 @@ static int build_codebook(hbx_pool* p, const std::vector<uint32_t>& freq) {
     RC(up((void**)&p->len_of_rank, lor.data(), lor.size()));
     RC(up((void**)&p->lut, lut.data(), lut.size() * 4));
     RC(up((void**)&p->dec, dec.data(), dec.size() * 4));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaStreamSynchronize(p->stream));
     p->has_cb = true;
     return HBX_OK;
 }
@@ -655,10 +664,13 @@ static int choose_shape(hbx_pool* p, Shape* out) {
         return HBX_OK;
     }
     auto key = std::make_pair(p->g->fingerprint, (int)p->model);
-    auto it = ctx->tuned.find(key);
-    if (it != ctx->tuned.end()) {
-        *out = it->second;
-        return HBX_OK;
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) {
+            *out = it->second;
+            return HBX_OK;
+        }
     }
     const Shape cands[] = {{64, 0, 1},      {128, 256, 1},  {128, 1024, 1}, {256, 4096, 1},
                            {128, 1024, 2},  {256, 1024, 2}, {256, 4096, 4}, {512, 4096, 1}};
@@ -674,13 +686,13 @@ static int choose_shape(hbx_pool* p, Shape* out) {
     const unsigned long long sc0 = p->hc.edges_scanned, lv0 = p->hc.edges_live;
     for (int rep = 0; rep < 2; rep++) {
         for (const Shape& sh : cands) {
-            CK(cudaEventRecord(e0, ctx->stream));
+            CK(cudaEventRecord(e0, p->stream));
             int r = run_sample(p, MODE_HIST, base, ncal, nullptr, freq, 0u, sh);
             if (r) {
                 dfree(ctx, freq);
                 return r;
             }
-            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventRecord(e1, p->stream));
             CK(cudaEventSynchronize(e1));
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, e0, e1));
@@ -696,7 +708,10 @@ static int choose_shape(hbx_pool* p, Shape* out) {
     cudaEventDestroy(e1);
     dfree(ctx, freq);
     p->device_bytes -= (size_t)p->g->n * 4;
-    ctx->tuned[key] = best;
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        ctx->tuned[key] = best;
+    }
     *out = best;
     return HBX_OK;
 }
@@ -721,8 +736,8 @@ static int ensure_codebook(hbx_pool* p) {
     p->aux_live += p->hc.edges_live - lv0;
     std::vector<uint32_t> hf(n);
     if (!r) {
-        cudaError_t e = cudaMemcpyAsync(hf.data(), freq, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        cudaError_t e = cudaMemcpyAsync(hf.data(), freq, (size_t)n * 4, cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
         if (e != cudaSuccess) r = cuda_fail(ctx, e, "warm-up histogram");
     }
     dfree(ctx, freq);
@@ -771,7 +786,7 @@ int pool_extend(hbx_pool* p, uint64_t T) {
         ia.bm_cap = (uint32_t)std::min<uint64_t>(p->bm_list_cap, 0xFFFFFFFFull);
         ia.ctr = p->ctr;
         ia.moments = p->moments;
-        CK(launch_index(ia, ctx->stream));
+        CK(launch_index(ia, p->stream));
         p->launches++;
         RC(read_counters(p));
         p->T = j0 + count;
@@ -847,17 +862,17 @@ int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* 
     RC(ensure_sel(p, T, k));
     const SelArgs a = sel_args(p, T);
     const uint32_t enc = p->o.encode;
-    CK(launch_sel_init(a, ctx->stream));
-    CK(launch_count(a, enc, ctx->stream));
+    CK(launch_sel_init(a, p->stream));
+    CK(launch_count(a, enc, p->stream));
     const uint64_t per_it = 3 + (enc ? (uint64_t)(a.has_cb ? 1 : 0) + (a.n_bm ? 1 : 0) : 1);
     p->launches += 1 + (enc ? (uint64_t)((a.n_items && a.has_cb) ? 1 : 0) + (a.n_bm ? 1 : 0) : 1) + per_it * k;
     if (p->o.form) {
         cudaGraph_t graph;
         cudaGraphExec_t exec;
-        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t le = cudaSuccess;
-        for (uint32_t it = 0; it < k && le == cudaSuccess; it++) le = launch_iteration(a, enc, ctx->stream);
-        cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+        for (uint32_t it = 0; it < k && le == cudaSuccess; it++) le = launch_iteration(a, enc, p->stream);
+        cudaError_t ce = cudaStreamEndCapture(p->stream, &graph);
         if (le != cudaSuccess) return cuda_fail(ctx, le, "selection capture");
         if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
         cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
@@ -865,8 +880,8 @@ int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* 
             cudaGraphDestroy(graph);
             return cuda_fail(ctx, ie, "cudaGraphInstantiate");
         }
-        cudaError_t le2 = cudaGraphLaunch(exec, ctx->stream);
-        cudaError_t se = cudaStreamSynchronize(ctx->stream);
+        cudaError_t le2 = cudaGraphLaunch(exec, p->stream);
+        cudaError_t se = cudaStreamSynchronize(p->stream);
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
         if (le2 != cudaSuccess) return cuda_fail(ctx, le2, "cudaGraphLaunch");
@@ -874,17 +889,17 @@ int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* 
     } else {
         SelState hs;
         for (uint32_t it = 0; it < k; it++) {
-            CK(launch_iteration(a, enc, ctx->stream));
-            CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
+            CK(launch_iteration(a, enc, p->stream));
+            CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, p->stream));
+            CK(cudaStreamSynchronize(p->stream));
         }
     }
     SelState hs;
     std::vector<unsigned long long> hm(k);
-    CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(seeds, p->d_seeds, (size_t)k * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(hm.data(), p->d_marg, (size_t)k * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(seeds, p->d_seeds, (size_t)k * 4, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(hm.data(), p->d_marg, (size_t)k * 8, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
     if (hs.pad) return fail(ctx, HBX_ERR_INTERNAL, "undecodable Huffman stream during selection");
     if (hs.it != k) return fail(ctx, HBX_ERR_INTERNAL, "selection ran " + std::to_string(hs.it) + " iterations");
     if (marginal)
@@ -921,6 +936,7 @@ extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint
     p->seed = seed;
     p->o = o;
     p->W = o.warmup_sets;
+    p->stream = ctx->stream;
     p->bp_words = (((uint64_t)g->n + 31) / 32 + 3) & ~3ull;
     int r = grow_buffer(p, (void**)&p->ctr, 0, sizeof(Counters), 0);
     if (!r) r = grow_buffer(p, (void**)&p->moments, 0, 3 * sizeof(double), 0);
@@ -928,6 +944,7 @@ extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint
         r = fail(ctx, HBX_ERR_CUDA, "cudaEventCreate");
     if (!r) {
         memset(&p->hc, 0, sizeof(p->hc));
+        std::lock_guard<std::mutex> lock(ctx->mu);
         ctx->pools.insert(p);
         *out = p;
         return HBX_OK;
@@ -942,7 +959,7 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
     if (!p) return;
     hbx_ctx* c = p->ctx;
     cudaSetDevice(c->device);
-    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(p->stream);
     void* bufs[] = {p->recs, p->raw.d, p->code.d, p->bm.d, p->ctr, p->moments, p->rank_of, p->vertex_of_rank,
                     p->code_of_rank, p->len_of_rank, p->lut, p->dec, p->items, p->bm_sets, p->big_list,
                     p->retry_list, p->list_in, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
@@ -951,7 +968,11 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
     for (void* b : bufs) dfree(c, b);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
-    c->pools.erase(p);
+    if (p->own_stream) cudaStreamDestroy(p->stream);
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        c->pools.erase(p);
+    }
     delete p;
 }
 
@@ -983,6 +1004,16 @@ namespace hbx {
 struct ImmBounds {
     double epsp, ellp, lnc, lambda_p, lambda_star;
 };
+
+static bool imm_bounds(uint32_t n, uint32_t k, double eps, double ell, ImmBounds* b);
+
+bool imm_lambda(uint32_t n, uint32_t k, double eps, double ell, double* lambda_p, double* lambda_star) {
+    ImmBounds b;
+    if (!imm_bounds(n, k, eps, ell, &b)) return false;
+    *lambda_p = b.lambda_p;
+    *lambda_star = b.lambda_star;
+    return true;
+}
 
 static bool imm_bounds(uint32_t n, uint32_t k, double eps, double ell, ImmBounds* b) {
     if (n < 2 || k == 0 || k > n || !(eps > 0.0 && eps < 1.0) || !(ell > 0.0)) return false;
@@ -1023,8 +1054,8 @@ void fill_stats(hbx_pool* p, hbx_stats* s) {
     s->warp_group_budget = p->shape.gb;
     s->block_cluster = p->shape.bc;
     double mom[3] = {0, 0, 0};
-    cudaMemcpyAsync(mom, p->moments, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->ctx->stream);
-    cudaStreamSynchronize(p->ctx->stream);
+    cudaMemcpyAsync(mom, p->moments, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    cudaStreamSynchronize(p->stream);
     // bytes held by the sets (heap words written) plus the 16-byte index per set
     s->pool_bytes = 4ull * p->hc.words_used + sizeof(SetRec) * p->T;
     s->raw_int32_bytes = 4ull * p->hc.rr_vertices + 8ull * p->T;
@@ -1144,14 +1175,14 @@ static int decode_range(hbx_pool* p, uint64_t j0, uint64_t j1, const uint64_t* o
     a.out = d_out;
     a.ends = d_end;
     a.ctr = p->ctr;
-    cudaError_t e = cudaMemcpyAsync(d_off, offsets, (cnt + 1) * 8, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_end, 0, cnt * 8, ctx->stream);
-    if (e == cudaSuccess) e = launch_decode(a, ctx->stream);
+    cudaError_t e = cudaMemcpyAsync(d_off, offsets, (cnt + 1) * 8, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_end, 0, cnt * 8, p->stream);
+    if (e == cudaSuccess) e = launch_decode(a, p->stream);
     p->launches++;
     if (e == cudaSuccess && offsets[cnt])
-        e = cudaMemcpyAsync(verts, d_out, offsets[cnt] * 4, cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess && ends) e = cudaMemcpyAsync(ends, d_end, cnt * 8, cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        e = cudaMemcpyAsync(verts, d_out, offsets[cnt] * 4, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess && ends) e = cudaMemcpyAsync(ends, d_end, cnt * 8, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     dfree(ctx, d_off);
     dfree(ctx, d_out);
     dfree(ctx, d_end);
@@ -1168,8 +1199,8 @@ extern "C" int hbx_pool_export_set(hbx_pool* p, uint64_t j, uint32_t* kind, uint
     if (j >= p->T) return fail(ctx, HBX_ERR_INVALID_ARG, "set id beyond the pool");
     cudaSetDevice(ctx->device);
     SetRec r;
-    CK(cudaMemcpyAsync(&r, p->recs + j, sizeof(r), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(&r, p->recs + j, sizeof(r), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
     const uint32_t k = rec_kind(r);
     const uint64_t off = rec_off(r);
     if (k == KIND_PENDING) return fail(ctx, HBX_ERR_INTERNAL, "set not written");
@@ -1195,21 +1226,21 @@ extern "C" int hbx_pool_export_set(hbx_pool* p, uint64_t j, uint32_t* kind, uint
         std::vector<uint32_t> words(cw + 1);
         if (cw)
             CK(cudaMemcpyAsync(words.data(), p->code.d + off + nside + nr, cw * 4, cudaMemcpyDeviceToHost,
-                               ctx->stream));
+                               p->stream));
         if (nr)
             CK(cudaMemcpyAsync(buf.data() + raw_at, p->code.d + off + nside, 4ull * nr, cudaMemcpyDeviceToHost,
-                               ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+                               p->stream));
+        CK(cudaStreamSynchronize(p->stream));
         memcpy(buf.data(), words.data(), cb);
     } else if (k == KIND_BITMAP) {
         const uint64_t nw = ((uint64_t)p->g->n + 31) / 32;
         buf.resize(nw * 4);
-        CK(cudaMemcpyAsync(buf.data(), p->bm.d + off, nw * 4, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpyAsync(buf.data(), p->bm.d + off, nw * 4, cudaMemcpyDeviceToHost, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
     } else {
         buf.resize(4ull * r.size);
-        CK(cudaMemcpyAsync(buf.data(), p->raw.d + off, 4ull * r.size, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpyAsync(buf.data(), p->raw.d + off, 4ull * r.size, cudaMemcpyDeviceToHost, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
     }
     if (nbytes) *nbytes = buf.size();
     if (buf.size() > cap || (!payload && buf.size()))
@@ -1227,8 +1258,8 @@ extern "C" int hbx_pool_decode_sets(hbx_pool* p, uint64_t j0, uint64_t j1, uint6
     const uint64_t cnt = j1 - j0;
     std::vector<SetRec> recs(cnt);
     if (cnt)
-        CK(cudaMemcpyAsync(recs.data(), p->recs + j0, cnt * sizeof(SetRec), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpyAsync(recs.data(), p->recs + j0, cnt * sizeof(SetRec), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
     offsets[0] = 0;
     for (uint64_t i = 0; i < cnt; i++) offsets[i + 1] = offsets[i] + recs[i].size;
     if (needed) *needed = offsets[cnt];

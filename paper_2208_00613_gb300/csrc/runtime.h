@@ -111,6 +111,10 @@ struct hbx_pool {
     uint64_t sample_kernel_launches = 0;
     uint64_t launches = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // stream of every launch and copy of this pool: the context's stream, or
+    // the pool's own one when a server runs pools side by side
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
 };
 
 namespace hbx {
@@ -123,6 +127,8 @@ int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* 
 int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds, double* influence,
                 uint64_t* marginal, hbx_stats* stats);
 void fill_stats(hbx_pool* p, hbx_stats* s);
+// lambda' and lambda* of the IMM bounds (false on bad arguments)
+bool imm_lambda(uint32_t n, uint32_t k, double eps, double ell, double* lambda_p, double* lambda_star);
 }  // namespace hbx
 
 void hbx_server_destroy_all(hbx_ctx* c);

@@ -279,39 +279,65 @@ __global__ void __launch_bounds__(SEL_THREADS) cover_kernel(SelArgs a) {
     const uint32_t u = a.st->u;
     const uint32_t ru = a.has_cb ? __ldg(a.cb.rank_of + u) : NONE;
     unsigned long long gain = 0;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < a.T; j += gridDim.x * blockDim.x) {
-        if (!a.alive[j]) continue;
-        const SetRec rec = a.recs[j];
-        const uint32_t kind = rec_kind(rec);
+    const uint32_t lane = threadIdx.x & 31;
+    // warp-uniform loop: every lane reaches the ballots below
+    for (uint32_t jb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); jb < a.T; jb += gridDim.x * blockDim.x) {
+        const uint32_t j = jb + lane;
         bool member = false;
-        if (kind == KIND_HUFF) {
-            const HuffView h = huff_view(a.code_heap, rec);
-            if (ru != NONE) member = huff_contains(a.cb, h, ru);
-            else member = sorted_contains(h.raw, h.n_raw, u);
-        } else if (kind == KIND_BITMAP) {
-            member = (__ldg(a.bm_heap + rec_off(rec) + (u >> 5)) >> (u & 31)) & 1u;
-        } else {
-            const uint32_t* x = a.raw_heap + rec_off(rec);
-            for (uint32_t i = 0; i < rec.size && !member; i++) member = __ldg(x + i) == u;
+        uint32_t kind = KIND_PENDING;
+        if (j < a.T && a.alive[j]) {
+            const SetRec rec = a.recs[j];
+            kind = rec_kind(rec);
+            if (kind == KIND_HUFF) {
+                const HuffView h = huff_view(a.code_heap, rec);
+                if (ru != NONE) member = huff_contains(a.cb, h, ru);
+                else member = sorted_contains(h.raw, h.n_raw, u);
+            } else if (kind == KIND_BITMAP) {
+                member = (__ldg(a.bm_heap + rec_off(rec) + (u >> 5)) >> (u & 31)) & 1u;
+            } else {
+                const uint32_t* x = a.raw_heap + rec_off(rec);
+                for (uint32_t i = 0; i < rec.size && !member; i++) member = __ldg(x + i) == u;
+            }
+            if (member) {
+                a.alive[j] = 0;
+                gain++;
+            }
         }
-        if (member) {
-            a.alive[j] = 0;
-            gain++;
-            if (kind == KIND_HUFF) a.cov_huff[atomicAdd(&a.st->n_cov_huff, 1u)] = j;
-            else if (kind == KIND_BITMAP) a.cov_bm[atomicAdd(&a.st->n_cov_bm, 1u)] = j;
-            else a.cov_raw[atomicAdd(&a.st->n_cov_raw, 1u)] = j;
+        // one list append per warp and kind
+#pragma unroll
+        for (uint32_t k = 0; k < 3; k++) {
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, member && kind == k);
+            if (!bal) continue;
+            uint32_t* list = k == KIND_HUFF ? a.cov_huff : (k == KIND_BITMAP ? a.cov_bm : a.cov_raw);
+            uint32_t* len = k == KIND_HUFF ? &a.st->n_cov_huff : (k == KIND_BITMAP ? &a.st->n_cov_bm : &a.st->n_cov_raw);
+            const uint32_t leader = __ffs(bal) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(len, (uint32_t)__popc(bal));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (member && kind == k) list[base + __popc(bal & lanemask_lt())] = j;
         }
     }
     gain = (unsigned long long)warp_sum((uint32_t)gain);
     if ((threadIdx.x & 31) == 0 && gain) atomicAdd(&a.st->gain, gain);
 }
 
-// Covered Huffman sets: one warp per set, lanes over 32-code chunks.
+// Covered Huffman sets: one warp per set, lanes over 32-code chunks.  The sets
+// covered in one iteration all hold u* and mostly the same frequent vertices,
+// so the lowest DEC_HOT ranks are decremented in a per-block shared-memory
+// histogram and flushed once per block instead of colliding in global memory.
+constexpr uint32_t DEC_HOT = 2048;
+
 __global__ void __launch_bounds__(SEL_THREADS) dec_huff_kernel(SelArgs a) {
+    __shared__ uint32_t hist[DEC_HOT];
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t wpb = blockDim.x >> 5;
+    const uint32_t nwarps = gridDim.x * wpb;
     const uint32_t len = a.st->n_cov_huff;
-    for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += nwarps) {
+    if (blockIdx.x * wpb >= len) return;  // no covered set for this block
+    const uint32_t hot = min(DEC_HOT, a.cb.nsym);
+    for (uint32_t i = threadIdx.x; i < hot; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < len; i += nwarps) {
         const HuffView h = huff_view(a.code_heap, a.recs[a.cov_huff[i]]);
         const uint32_t nch = (h.n_coded + 31) / 32;
         for (uint32_t c = lane; c < nch; c += 32) {
@@ -319,10 +345,16 @@ __global__ void __launch_bounds__(SEL_THREADS) dec_huff_kernel(SelArgs a) {
             const uint32_t cnt = min(32u, h.n_coded - 32 * c);
             for (uint32_t k = 0; k < cnt; k++) {
                 const uint32_t r = decode_one_g(a.cb, h.words, pos);
-                if (r != NONE) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -1);
+                if (r < hot) atomicAdd(&hist[r], 1u);
+                else if (r != NONE) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -1);
             }
         }
         for (uint32_t k = lane; k < h.n_raw; k += 32) atomicAdd(&a.cnt[__ldg(h.raw + k)], -1);
+    }
+    __syncthreads();
+    for (uint32_t r = threadIdx.x; r < hot; r += blockDim.x) {
+        const uint32_t x = hist[r];
+        if (x) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -(int)x);
     }
 }
 

@@ -1,0 +1,97 @@
+"""Serving loop: continuous batching over resident graphs and RR pools.
+
+Every query's result in the mix (queries arriving while others run, pools
+shared and extended across queries, several pools in flight on their own
+streams) must equal the same query run alone through hbx_imm: seeds and the
+FP64 influence estimate, exactly.  Also: cancellation of a queued query, a
+bounded wait that runs out, and admission rejection by projected footprint.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+hbx = pytest.importorskip("paper_2208_00613_gb300")
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    hbx.build()
+    tc = hbx.torch_context(0)
+    gs = []
+    for n, m, seed, wc in [(4096, 32768, 1, False), (1 << 15, 1 << 18, 5, True), (1 << 16, 1 << 19, 6, False)]:
+        g = synth.rmat(n, m, seed)
+        g.prob = synth.weighted_cascade(g) if wc else synth.ic_uniform(g, seed, 0.1)
+        g.lt_weight = synth.lt_weights(g, seed)
+        gs.append(g)
+    handles = [hbx.hbx_graph_create(tc.ctx, g) for g in gs]
+    yield tc, gs, handles
+    for h in handles:
+        hbx.hbx_graph_destroy(h)
+    tc.close()
+
+
+def test_mix_equals_alone(env):
+    tc, gs, handles = env
+    qs = synth.poisson_queries(seed=3, count=16, rate_per_s=200.0, graphs=[0, 1, 2], k_range=(5, 40),
+                               eps_choices=(0.3, 0.5))
+    alone = []
+    for q in qs:
+        r = hbx.hbx_imm(tc.ctx, handles[q["graph"]], q["model"], q["k"], q["eps"], 1.0, 7)
+        alone.append(r)
+    srv = hbx.hbx_server_create(tc.ctx, 3, 0)
+    try:
+        tickets = []
+        t0 = time.perf_counter()
+        for q in qs:
+            while time.perf_counter() - t0 < q["t"]:
+                time.sleep(0.001)
+            tickets.append(hbx.hbx_submit(tc.ctx, srv, handles[q["graph"]], q["model"], q["k"], q["eps"], 1.0, 7))
+        lat = []
+        for q, t, ref in zip(qs, tickets, alone):
+            rc, res = hbx.hbx_wait(t, q["k"])
+            hbx.hbx_ticket_destroy(t)
+            assert rc == 0, hbx.hbx_strerror(rc)
+            assert np.array_equal(res["seeds"], ref["seeds"]), q
+            assert res["influence"] == ref["influence"], q
+            assert res["stats"]["theta"] == ref["stats"]["theta"], q
+            lat.append(res["latency_s"])
+        lat = np.array(lat)
+        print(f"served {len(qs)} queries: p50 {np.percentile(lat, 50) * 1e3:.1f} ms, "
+              f"p99 {np.percentile(lat, 99) * 1e3:.1f} ms")
+    finally:
+        hbx.hbx_server_destroy(srv)
+
+
+def test_cancel_timeout_admission(env):
+    tc, gs, handles = env
+    srv = hbx.hbx_server_create(tc.ctx, 1, 0)
+    try:
+        first = hbx.hbx_submit(tc.ctx, srv, handles[1], "IC", 200, 0.2, 1.0, 11)
+        second = hbx.hbx_submit(tc.ctx, srv, handles[1], "IC", 10, 0.5, 1.0, 12)
+        rc, _ = hbx.hbx_wait(second, 10, timeout_us=0)
+        assert rc in (-4, 0)  # still waiting behind the first query (or already done)
+        crc = hbx.hbx_cancel(second)
+        rc, _ = hbx.hbx_wait(second, 10)
+        if crc == 0:
+            assert rc == -7
+        rc, res = hbx.hbx_wait(first, 200)
+        assert rc == 0
+        hbx.hbx_ticket_destroy(first)
+        hbx.hbx_ticket_destroy(second)
+    finally:
+        hbx.hbx_server_destroy(srv)
+    tiny = hbx.hbx_server_create(tc.ctx, 1, 1 << 20)
+    try:
+        with pytest.raises(hbx.HbxError) as e:
+            hbx.hbx_submit(tc.ctx, tiny, handles[2], "IC", 50, 0.1, 1.0, 1)
+        assert e.value.code == -6
+    finally:
+        hbx.hbx_server_destroy(tiny)
