@@ -20,6 +20,7 @@ struct SelState {
     uint32_t n_cov_huff, n_cov_bm, n_cov_raw, pad;
     unsigned long long gain;     // sets covered by u* this iteration
     unsigned long long covered;  // total covered
+    unsigned long long n_dec;    // chunk items of the Huffman sets covered this iteration
 };
 
 struct SelArgs {
@@ -41,6 +42,8 @@ struct SelArgs {
     uint32_t* cov_huff;                    // sets covered this iteration, by kind
     uint32_t* cov_bm;
     uint32_t* cov_raw;
+    unsigned long long* dec_items;         // (j << 32) | chunk of covered Huffman sets
+    unsigned long long dec_cap;
     unsigned long long* partials;          // argmax per-block results
     unsigned int* ticket;
     uint32_t* seeds;                       // [k]

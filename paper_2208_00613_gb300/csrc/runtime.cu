@@ -814,6 +814,12 @@ static int ensure_sel(hbx_pool* p, uint64_t T, uint32_t k) {
         RC(grow_buffer(p, (void**)&p->cov_raw, p->alive_cap * 4, nc * 4, 0));
         p->alive_cap = nc;
     }
+    if (p->hc.chunk_items > p->dec_cap) {
+        // the sets covered in one iteration hold at most every chunk of the pool
+        const uint64_t nc = std::max<uint64_t>(p->hc.chunk_items, p->dec_cap * 2);
+        RC(grow_buffer(p, (void**)&p->dec_items, p->dec_cap * 8, nc * 8, 0));
+        p->dec_cap = nc;
+    }
     if (k > p->kcap) {
         RC(grow_buffer(p, (void**)&p->d_seeds, p->kcap * 4, (size_t)k * 4, 0));
         RC(grow_buffer(p, (void**)&p->d_marg, p->kcap * 8, (size_t)k * 8, 0));
@@ -845,6 +851,8 @@ static SelArgs sel_args(hbx_pool* p, uint64_t T) {
     a.cov_huff = p->cov_huff;
     a.cov_bm = p->cov_bm;
     a.cov_raw = p->cov_raw;
+    a.dec_items = p->dec_items;
+    a.dec_cap = p->dec_cap;
     a.partials = p->partials;
     a.ticket = p->ticket;
     a.seeds = p->d_seeds;
@@ -853,26 +861,28 @@ static SelArgs sel_args(hbx_pool* p, uint64_t T) {
     return a;
 }
 
-int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* marginal, uint64_t* covered) {
+// Launch greedy selection on sets [0, T) on stream `st` without waiting.  The
+// persistent form replays the k iterations from one CUDA graph; the plain form
+// launches them one by one and reads u* back after each.
+static int pool_select_launch(hbx_pool* p, uint64_t T, uint32_t k, cudaStream_t st) {
     hbx_ctx* ctx = p->ctx;
     if (T == 0 || T > p->T) return fail(ctx, HBX_ERR_INVALID_ARG, "T must be in [1, pool size]");
     if (k == 0 || k > p->g->n) return fail(ctx, HBX_ERR_INVALID_ARG, "k must be in [1, n]");
     cudaSetDevice(ctx->device);
-    const double t0 = now_s();
     RC(ensure_sel(p, T, k));
     const SelArgs a = sel_args(p, T);
     const uint32_t enc = p->o.encode;
-    CK(launch_sel_init(a, p->stream));
-    CK(launch_count(a, enc, p->stream));
+    CK(launch_sel_init(a, st));
+    CK(launch_count(a, enc, st));
     const uint64_t per_it = 3 + (enc ? (uint64_t)(a.has_cb ? 1 : 0) + (a.n_bm ? 1 : 0) : 1);
     p->launches += 1 + (enc ? (uint64_t)((a.n_items && a.has_cb) ? 1 : 0) + (a.n_bm ? 1 : 0) : 1) + per_it * k;
     if (p->o.form) {
         cudaGraph_t graph;
         cudaGraphExec_t exec;
-        CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         cudaError_t le = cudaSuccess;
-        for (uint32_t it = 0; it < k && le == cudaSuccess; it++) le = launch_iteration(a, enc, p->stream);
-        cudaError_t ce = cudaStreamEndCapture(p->stream, &graph);
+        for (uint32_t it = 0; it < k && le == cudaSuccess; it++) le = launch_iteration(a, enc, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
         if (le != cudaSuccess) return cuda_fail(ctx, le, "selection capture");
         if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
         cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
@@ -880,31 +890,44 @@ int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* 
             cudaGraphDestroy(graph);
             return cuda_fail(ctx, ie, "cudaGraphInstantiate");
         }
-        cudaError_t le2 = cudaGraphLaunch(exec, p->stream);
-        cudaError_t se = cudaStreamSynchronize(p->stream);
-        cudaGraphExecDestroy(exec);
+        cudaError_t le2 = cudaGraphLaunch(exec, st);
+        cudaGraphExecDestroy(exec);  // released once the launched work completes
         cudaGraphDestroy(graph);
         if (le2 != cudaSuccess) return cuda_fail(ctx, le2, "cudaGraphLaunch");
-        if (se != cudaSuccess) return cuda_fail(ctx, se, "selection");
     } else {
         SelState hs;
         for (uint32_t it = 0; it < k; it++) {
-            CK(launch_iteration(a, enc, p->stream));
-            CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, p->stream));
-            CK(cudaStreamSynchronize(p->stream));
+            CK(launch_iteration(a, enc, st));
+            CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
         }
     }
+    return HBX_OK;
+}
+
+// Wait for the selection launched on `st` and read its results.
+static int pool_select_finish(hbx_pool* p, uint32_t k, uint32_t* seeds, uint64_t* marginal, uint64_t* covered,
+                              cudaStream_t st) {
+    hbx_ctx* ctx = p->ctx;
     SelState hs;
     std::vector<unsigned long long> hm(k);
-    CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaMemcpyAsync(seeds, p->d_seeds, (size_t)k * 4, cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaMemcpyAsync(hm.data(), p->d_marg, (size_t)k * 8, cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
-    if (hs.pad) return fail(ctx, HBX_ERR_INTERNAL, "undecodable Huffman stream during selection");
+    CK(cudaMemcpyAsync(&hs, p->st, sizeof(SelState), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(seeds, p->d_seeds, (size_t)k * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hm.data(), p->d_marg, (size_t)k * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hs.pad == 1) return fail(ctx, HBX_ERR_INTERNAL, "undecodable Huffman stream during selection");
+    if (hs.pad) return fail(ctx, HBX_ERR_INTERNAL, "decrement item list overflow during selection");
     if (hs.it != k) return fail(ctx, HBX_ERR_INTERNAL, "selection ran " + std::to_string(hs.it) + " iterations");
     if (marginal)
         for (uint32_t i = 0; i < k; i++) marginal[i] = hm[i];
     if (covered) *covered = hs.covered;
+    return HBX_OK;
+}
+
+int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* marginal, uint64_t* covered) {
+    const double t0 = now_s();
+    RC(pool_select_launch(p, T, k, p->stream));
+    RC(pool_select_finish(p, k, seeds, marginal, covered, p->stream));
     p->select_s += now_s() - t0;
     return HBX_OK;
 }
@@ -964,7 +987,7 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
                     p->code_of_rank, p->len_of_rank, p->lut, p->dec, p->items, p->bm_sets, p->big_list,
                     p->retry_list, p->list_in, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
                     p->alive, p->cov_huff, p->cov_bm, p->cov_raw, p->st, p->partials, p->ticket, p->d_seeds,
-                    p->d_marg};
+                    p->d_marg, p->dec_items};
     for (void* b : bufs) dfree(c, b);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);

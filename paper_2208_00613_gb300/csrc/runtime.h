@@ -100,6 +100,8 @@ struct hbx_pool {
     uint8_t* alive = nullptr;
     uint64_t alive_cap = 0;
     uint32_t *cov_huff = nullptr, *cov_bm = nullptr, *cov_raw = nullptr;
+    unsigned long long* dec_items = nullptr;  // chunk items of the sets covered in one iteration
+    uint64_t dec_cap = 0;
     void* st = nullptr;
     unsigned long long* partials = nullptr;
     unsigned int* ticket = nullptr;

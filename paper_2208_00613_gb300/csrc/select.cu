@@ -62,18 +62,25 @@ __global__ void sel_init_kernel(SelArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         SelState z;
         z.u = NONE; z.it = 0; z.n_cov_huff = 0; z.n_cov_bm = 0; z.n_cov_raw = 0; z.pad = 0; z.gain = 0; z.covered = 0;
+        z.n_dec = 0;
         *a.st = z;
         *a.ticket = 0;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Initial count over Huffman chunks: one thread decodes one 32-code chunk (or
-// reads 32 copy-array ids).  Hot ranks go to a shared-memory histogram, the
-// rest to cnt, with one atomic per group of lanes hitting the same counter.
+// Count (sign +1, over every chunk of the pool) or decrement (sign -1, over the
+// chunks of the sets covered this iteration): one thread decodes one 32-code
+// chunk (or reads 32 copy-array ids).  Hot ranks go to a shared-memory
+// histogram, the rest to cnt, with one atomic per group of lanes hitting the
+// same counter.  The item count comes from the device (n_dev) or the host.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(COUNT_THREADS) count_huff_kernel(SelArgs a) {
+__global__ void __launch_bounds__(COUNT_THREADS) count_items_kernel(SelArgs a, const unsigned long long* items,
+                                                                   const unsigned long long* n_dev,
+                                                                   unsigned long long n_host, int sign) {
     extern __shared__ __align__(16) uint32_t smem[];
+    const unsigned long long n_items = n_dev ? *n_dev : n_host;
+    if ((unsigned long long)blockIdx.x * blockDim.x >= n_items) return;  // no item for this block
     DecodeSmem& ds = *reinterpret_cast<DecodeSmem*>(smem);
     uint32_t* hist = smem + sizeof(DecodeSmem) / 4;
     load_decode_smem(ds, a.cb);
@@ -82,14 +89,14 @@ __global__ void __launch_bounds__(COUNT_THREADS) count_huff_kernel(SelArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (unsigned long long wb = (unsigned long long)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
-         wb < a.n_items; wb += nwarps * 32) {
+         wb < n_items; wb += nwarps * 32) {
         const unsigned long long t = wb + lane;
         uint32_t ncodes = 0, is_code = 0;
         uint64_t pos = 0;
         const uint32_t* words = nullptr;
         const uint32_t* raw = nullptr;
-        if (t < a.n_items) {
-            const unsigned long long item = a.chunk_items[t];
+        if (t < n_items) {
+            const unsigned long long item = items[t];
             const uint32_t j = (uint32_t)(item >> 32), c = (uint32_t)item;
             if (j < a.T) {
                 const HuffView h = huff_view(a.code_heap, a.recs[j]);
@@ -121,7 +128,7 @@ __global__ void __launch_bounds__(COUNT_THREADS) count_huff_kernel(SelArgs a) {
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, target);
             if (have && target != NONE && lane == (uint32_t)(__ffs(peers) - 1)) {
                 const uint32_t c = __popc(peers);
-                if (target & RAW_FLAG) atomicAdd(&a.cnt[target & ~RAW_FLAG], (int)c);
+                if (target & RAW_FLAG) atomicAdd(&a.cnt[target & ~RAW_FLAG], sign * (int)c);
                 else atomicAdd(&hist[target], c);
             }
             if (__all_sync(0xFFFFFFFFu, i + 1 >= ncodes)) break;
@@ -130,7 +137,7 @@ __global__ void __launch_bounds__(COUNT_THREADS) count_huff_kernel(SelArgs a) {
     __syncthreads();
     for (uint32_t r = threadIdx.x; r < a.hot; r += blockDim.x) {
         const uint32_t h = hist[r];
-        if (h) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], (int)h);
+        if (h) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], sign * (int)h);
     }
 }
 
@@ -284,10 +291,11 @@ __global__ void __launch_bounds__(SEL_THREADS) cover_kernel(SelArgs a) {
     for (uint32_t jb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); jb < a.T; jb += gridDim.x * blockDim.x) {
         const uint32_t j = jb + lane;
         bool member = false;
-        uint32_t kind = KIND_PENDING;
+        uint32_t kind = KIND_PENDING, nit = 0;
         if (j < a.T && a.alive[j]) {
             const SetRec rec = a.recs[j];
             kind = rec_kind(rec);
+            nit = (rec.n_coded + 31) / 32 + (rec.size - rec.n_coded + 31) / 32;
             if (kind == KIND_HUFF) {
                 const HuffView h = huff_view(a.code_heap, rec);
                 if (ru != NONE) member = huff_contains(a.cb, h, ru);
@@ -316,46 +324,24 @@ __global__ void __launch_bounds__(SEL_THREADS) cover_kernel(SelArgs a) {
             base = __shfl_sync(0xFFFFFFFFu, base, leader);
             if (member && kind == k) list[base + __popc(bal & lanemask_lt())] = j;
         }
+        // chunk items of the covered Huffman sets, for the decrement pass
+        if (!(member && kind == KIND_HUFF)) nit = 0;
+        const uint32_t incl = warp_incl_scan(nit);
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (tot) {
+            unsigned long long base = 0;
+            if (lane == 31) base = atomicAdd(&a.st->n_dec, (unsigned long long)tot);
+            base = __shfl_sync(0xFFFFFFFFu, base, 31);
+            const unsigned long long my = base + incl - nit;
+            if (my + nit <= a.dec_cap) {
+                for (uint32_t c = 0; c < nit; c++) a.dec_items[my + c] = ((unsigned long long)j << 32) | c;
+            } else if (nit) {
+                atomicMax(&a.st->pad, 2u);
+            }
+        }
     }
     gain = (unsigned long long)warp_sum((uint32_t)gain);
     if ((threadIdx.x & 31) == 0 && gain) atomicAdd(&a.st->gain, gain);
-}
-
-// Covered Huffman sets: one warp per set, lanes over 32-code chunks.  The sets
-// covered in one iteration all hold u* and mostly the same frequent vertices,
-// so the lowest DEC_HOT ranks are decremented in a per-block shared-memory
-// histogram and flushed once per block instead of colliding in global memory.
-constexpr uint32_t DEC_HOT = 2048;
-
-__global__ void __launch_bounds__(SEL_THREADS) dec_huff_kernel(SelArgs a) {
-    __shared__ uint32_t hist[DEC_HOT];
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t wpb = blockDim.x >> 5;
-    const uint32_t nwarps = gridDim.x * wpb;
-    const uint32_t len = a.st->n_cov_huff;
-    if (blockIdx.x * wpb >= len) return;  // no covered set for this block
-    const uint32_t hot = min(DEC_HOT, a.cb.nsym);
-    for (uint32_t i = threadIdx.x; i < hot; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    for (uint32_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < len; i += nwarps) {
-        const HuffView h = huff_view(a.code_heap, a.recs[a.cov_huff[i]]);
-        const uint32_t nch = (h.n_coded + 31) / 32;
-        for (uint32_t c = lane; c < nch; c += 32) {
-            uint64_t pos = c ? __ldg(h.side + c - 1) : 0u;
-            const uint32_t cnt = min(32u, h.n_coded - 32 * c);
-            for (uint32_t k = 0; k < cnt; k++) {
-                const uint32_t r = decode_one_g(a.cb, h.words, pos);
-                if (r < hot) atomicAdd(&hist[r], 1u);
-                else if (r != NONE) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -1);
-            }
-        }
-        for (uint32_t k = lane; k < h.n_raw; k += 32) atomicAdd(&a.cnt[__ldg(h.raw + k)], -1);
-    }
-    __syncthreads();
-    for (uint32_t r = threadIdx.x; r < hot; r += blockDim.x) {
-        const uint32_t x = hist[r];
-        if (x) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -(int)x);
-    }
 }
 
 __global__ void __launch_bounds__(SEL_THREADS) dec_raw_kernel(SelArgs a) {
@@ -379,6 +365,7 @@ __global__ void finalize_kernel(SelArgs a) {
     s.n_cov_huff = 0;
     s.n_cov_bm = 0;
     s.n_cov_raw = 0;
+    s.n_dec = 0;
     *a.st = s;
 }
 
@@ -398,12 +385,19 @@ cudaError_t launch_count(const SelArgs& a, uint32_t encode, cudaStream_t s) {
         count_raw_kernel<<<sh.count_blocks * 2, SEL_THREADS, 0, s>>>(a);
         return cudaGetLastError();
     }
+    if (a.has_cb) {
+        // the kernel's largest shared-memory footprint, the same value from every
+        // pool and thread (a per-pool value could race with another pool's
+        // launch); also covers the decrement launches captured after this
+        const size_t smem_max = sizeof(DecodeSmem) + (size_t)HOT_RANKS * 4;
+        cudaError_t e =
+            cudaFuncSetAttribute(count_items_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+        if (e != cudaSuccess) return e;
+    }
     if (a.n_items && a.has_cb) {
         const size_t smem = sizeof(DecodeSmem) + (size_t)a.hot * 4;
-        cudaError_t e = cudaFuncSetAttribute(count_huff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        count_huff_kernel<<<sh.count_blocks, COUNT_THREADS, smem, s>>>(a);
-        e = cudaGetLastError();
+        count_items_kernel<<<sh.count_blocks, COUNT_THREADS, smem, s>>>(a, a.chunk_items, nullptr, a.n_items, 1);
+        const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (a.n_bm) {
@@ -425,7 +419,9 @@ cudaError_t launch_iteration(const SelArgs& a, uint32_t encode, cudaStream_t s) 
     argmax_kernel<<<sh.argmax_blocks, SEL_THREADS, 0, s>>>(a);
     cover_kernel<<<cover_blocks ? cover_blocks : 1u, SEL_THREADS, 0, s>>>(a);
     if (encode) {
-        if (a.has_cb) dec_huff_kernel<<<(uint32_t)a.sms, SEL_THREADS, 0, s>>>(a);
+        if (a.has_cb)
+            count_items_kernel<<<sh.count_blocks, COUNT_THREADS, sizeof(DecodeSmem) + (size_t)a.hot * 4, s>>>(
+                a, a.dec_items, &a.st->n_dec, 0, -1);
         if (a.n_bm) bitmap_count_kernel<<<sh.dec_blocks, SEL_THREADS, 0, s>>>(a, a.cov_bm, &a.st->n_cov_bm, 0, -1);
     } else {
         dec_raw_kernel<<<sh.dec_blocks, SEL_THREADS, 0, s>>>(a);

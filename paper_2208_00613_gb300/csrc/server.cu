@@ -54,6 +54,7 @@ struct Query {
     hbx_stats stats{};
     double t_submit = 0, t_done = 0;
     uint64_t projected = 0;
+    std::string error;  // message of a failed query
 };
 
 using PoolKey = std::tuple<const hbx_graph*, int, uint64_t, uint32_t, uint32_t, uint32_t, uint32_t>;
@@ -186,6 +187,10 @@ void worker(hbx_server* s) {
         e2.last_used = now_s();
         if (rc == HBX_OK) e2.last_lb = std::max(e2.last_lb, q->stats.lb);
         q->rc = rc;
+        if (rc != HBX_OK) {
+            std::lock_guard<std::mutex> elock(s->ctx->mu);
+            q->error = s->ctx->last_error;
+        }
         q->t_done = now_s();
         q->state = Q_DONE;
         s->cv_done.notify_all();
@@ -299,7 +304,10 @@ extern "C" int hbx_wait(hbx_ticket* t, uint32_t* seeds_out, double* influence_ou
     else if (!s->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), done)) return HBX_ERR_TIMEOUT;
     Query& q = *t->q;
     if (q.state == Q_CANCELLED) return HBX_ERR_CANCELLED;
-    if (q.rc != HBX_OK) return q.rc;
+    if (q.rc != HBX_OK) {
+        fail(s->ctx, q.rc, q.error);  // the query's own message becomes the context's last error
+        return q.rc;
+    }
     if (seeds_out) std::copy(q.seeds.begin(), q.seeds.end(), seeds_out);
     if (influence_out) *influence_out = q.influence;
     if (stats_out) *stats_out = q.stats;

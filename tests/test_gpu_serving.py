@@ -58,7 +58,7 @@ def test_mix_equals_alone(env):
         for q, t, ref in zip(qs, tickets, alone):
             rc, res = hbx.hbx_wait(t, q["k"])
             hbx.hbx_ticket_destroy(t)
-            assert rc == 0, hbx.hbx_strerror(rc)
+            assert rc == 0, (hbx.hbx_strerror(rc), hbx.hbx_last_error(tc.ctx))
             assert np.array_equal(res["seeds"], ref["seeds"]), q
             assert res["influence"] == ref["influence"], q
             assert res["stats"]["theta"] == ref["stats"]["theta"], q
