@@ -85,7 +85,9 @@ struct Counters {
     unsigned long long error;
     unsigned long long chunk_items, bm_list;  // selection indexes
     unsigned long long words_used;            // heap words held by emitted sets
-    unsigned long long pad[12];
+    unsigned long long mid_work;              // work-stealing cursor of the shared-memory block kernel
+    unsigned long long giant_count;           // sets too large for shared memory
+    unsigned long long pad[10];
 };
 
 struct SampleArgs {
@@ -107,6 +109,7 @@ struct SampleArgs {
     DevCodebook cb;
     uint32_t* big_list;       // sets larger than a warp's capacity
     uint32_t* retry_list;     // sets whose heap space ran out
+    uint32_t* giant_list;     // sets larger than a block's shared memory holds
     Counters* ctr;
     // block-per-set scratch, one slot per resident block
     uint32_t* bp_visited;     // slots x bp_words

@@ -10,6 +10,7 @@ namespace hbx {
 
 // ---- sampling (sample.cu) ----
 cudaError_t launch_sample_warp(const SampleArgs& a, uint32_t qw, int sms, cudaStream_t s);
+cudaError_t launch_sample_mid(const SampleArgs& a, uint32_t nbig, int sms, cudaStream_t s);
 cudaError_t launch_sample_block(const SampleArgs& a, uint32_t nbig, uint32_t slots, uint32_t csize, cudaStream_t s);
 int block_path_max_clusters(uint32_t csize);
 

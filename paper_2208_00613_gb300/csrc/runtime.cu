@@ -387,6 +387,7 @@ static int ensure_lists(hbx_pool* p, uint64_t count) {
     RC(grow_buffer(p, (void**)&p->big_list, p->list_cap * 4, nc * 4, 0));
     RC(grow_buffer(p, (void**)&p->retry_list, p->list_cap * 4, nc * 4, 0));
     RC(grow_buffer(p, (void**)&p->list_in, p->list_cap * 4, nc * 4, 0));
+    RC(grow_buffer(p, (void**)&p->giant_list, p->list_cap * 4, nc * 4, 0));
     p->list_cap = nc;
     return HBX_OK;
 }
@@ -416,6 +417,7 @@ static int reset_launch_counters(hbx_pool* p) {
     hbx_ctx* ctx = p->ctx;
     CK(cudaMemsetAsync(p->ctr, 0, 2 * sizeof(unsigned long long), p->stream));  // work, big_work
     CK(cudaMemsetAsync(&p->ctr->big_count, 0, 2 * sizeof(unsigned long long), p->stream));
+    CK(cudaMemsetAsync(&p->ctr->mid_work, 0, 2 * sizeof(unsigned long long), p->stream));  // + giant_count
     return HBX_OK;
 }
 
@@ -446,6 +448,7 @@ static SampleArgs sample_args(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t 
     a.cb = dev_codebook(p);
     a.big_list = p->big_list;
     a.retry_list = p->retry_list;
+    a.giant_list = p->giant_list;
     a.ctr = p->ctr;
     a.bp_visited = p->bp_visited;
     a.bp_rbits = p->bp_rbits;
@@ -477,10 +480,26 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
             p->sample_kernel_s += ms * 1e-3;
             p->sample_kernel_launches++;
         }
-        const uint32_t nbig = (uint32_t)p->hc.big_count;
+        const uint32_t nmid = (uint32_t)p->hc.big_count;
+        if (nmid) {
+            // sets that outgrew a warp: one block each, held in shared memory
+            if (timed) CK(cudaEventRecord(p->ev0, p->stream));
+            CK(launch_sample_mid(a, nmid, ctx->sms, p->stream));
+            if (timed) CK(cudaEventRecord(p->ev1, p->stream));
+            p->launches++;
+            RC(read_counters(p));
+            if (timed) {
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+                p->sample_kernel_s += ms * 1e-3;
+                p->sample_kernel_launches++;
+            }
+        }
+        const uint32_t nbig = (uint32_t)p->hc.giant_count;
         if (nbig) {
-            // one scratch slot (visited, rank and aux bitmaps + an n-entry queue) per
-            // resident block, at most 8 GB of slots
+            // sets that outgrew shared memory: one block or cluster each, with an
+            // n-bit visited bitmap and an n-entry queue in HBM (one scratch slot
+            // per resident cluster, at most 8 GB of slots)
             const uint64_t slot_bytes = p->bp_words * 12 + (uint64_t)p->g->n * 4;
             const uint64_t mem_slots = std::max<uint64_t>(1, (8ull << 30) / slot_bytes);
             const uint32_t csize = sh.bc ? sh.bc : 1u;
@@ -488,6 +507,7 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
             slots = (uint32_t)std::min<uint64_t>(slots, std::max<uint64_t>(mem_slots, p->bp_slots));
             RC(ensure_block_scratch(p, slots));
             a = sample_args(p, mode, j0, count, list, freq, cut, sh);
+            a.big_list = p->giant_list;
             if (timed) CK(cudaEventRecord(p->ev0, p->stream));
             CK(launch_sample_block(a, nbig, slots, csize, p->stream));
             if (timed) CK(cudaEventRecord(p->ev1, p->stream));
@@ -985,7 +1005,7 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
     cudaStreamSynchronize(p->stream);
     void* bufs[] = {p->recs, p->raw.d, p->code.d, p->bm.d, p->ctr, p->moments, p->rank_of, p->vertex_of_rank,
                     p->code_of_rank, p->len_of_rank, p->lut, p->dec, p->items, p->bm_sets, p->big_list,
-                    p->retry_list, p->list_in, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
+                    p->retry_list, p->list_in, p->giant_list, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
                     p->alive, p->cov_huff, p->cov_bm, p->cov_raw, p->st, p->partials, p->ticket, p->d_seeds,
                     p->d_marg, p->dec_items};
     for (void* b : bufs) dfree(c, b);

@@ -89,7 +89,7 @@ struct hbx_pool {
     uint32_t* bm_sets = nullptr;
     uint64_t bm_list_cap = 0;
     // sampling lists
-    uint32_t *big_list = nullptr, *retry_list = nullptr, *list_in = nullptr;
+    uint32_t *big_list = nullptr, *retry_list = nullptr, *list_in = nullptr, *giant_list = nullptr;
     uint64_t list_cap = 0;
     // block-path scratch
     uint32_t *bp_visited = nullptr, *bp_rbits = nullptr, *bp_aux = nullptr, *bp_queue = nullptr;

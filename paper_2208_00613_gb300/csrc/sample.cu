@@ -917,6 +917,326 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
 }
 
 // ---------------------------------------------------------------------------
+// Shared-memory block path: one 512-thread block per set that outgrew a warp,
+// for sets of up to BQ vertices.  The vertex list, each vertex's CSR bounds
+// (loaded when the vertex is discovered, so the next level does not wait for
+// them) and the visited hash set all live in shared memory; a BFS level costs
+// one block-wide scan of group counts and one barrier per 512 frontier
+// vertices.  A set that outgrows BQ goes to the global-bitmap block kernel.
+// ---------------------------------------------------------------------------
+constexpr uint32_t BQ = 4096;
+constexpr uint32_t BQ_HASH = 2 * BQ;
+
+struct MidShared {
+    uint32_t scan[BP_THREADS];
+    uint32_t g0[BP_THREADS];
+    uint32_t eb[BP_THREADS];
+    uint32_t ee[BP_THREADS];
+    uint32_t warp[33];
+    uint32_t stage[40];
+    uint32_t tail, item;
+    int overflow, fail;
+};
+
+constexpr size_t MID_DYN_SMEM = (size_t)(3 * BQ + BQ_HASH) * sizeof(uint32_t);
+
+__device__ __forceinline__ void mid_append(const SampleArgs& a, MidShared& s, uint32_t* Q, uint32_t* QB,
+                                           uint32_t* QE, bool isnew, uint32_t u) {
+    const uint32_t lane = lane_id();
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isnew);
+    if (!bal) return;
+    const uint32_t leader = __ffs(bal) - 1;
+    uint32_t pos = 0;
+    if (lane == leader) pos = atomicAdd(&s.tail, (uint32_t)__popc(bal));
+    pos = __shfl_sync(0xFFFFFFFFu, pos, leader) + __popc(bal & lanemask_lt());
+    if (isnew) {
+        if (pos < BQ) {
+            Q[pos] = u;
+            QB[pos] = __ldg(a.g.row_ptr + u);
+            QE[pos] = __ldg(a.g.row_ptr + u + 1);
+        } else {
+            s.overflow = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BP_THREADS) sample_mid_kernel(SampleArgs a, uint32_t nbig) {
+    extern __shared__ __align__(16) uint32_t mdyn[];
+    __shared__ MidShared s;
+    uint32_t* Q = mdyn;
+    uint32_t* QB = Q + BQ;
+    uint32_t* QE = QB + BQ;
+    uint32_t* H = QE + BQ;
+    constexpr uint32_t HMASK = BQ_HASH - 1;
+    constexpr uint32_t HSHIFT = 32 - __builtin_ctz(BQ_HASH);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t n = a.g.n;
+    unsigned long long scanned = 0, live = 0;  // emitted sets only
+    for (uint32_t i = tid; i < BQ_HASH / 4; i += BP_THREADS) reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
+
+    for (;;) {
+        unsigned long long set_scanned = 0, set_live = 0;
+        if (tid == 0) s.item = (uint32_t)min(atomicAdd(&a.ctr->mid_work, 1ull), (unsigned long long)nbig);
+        __syncthreads();
+        const uint32_t item = s.item;
+        if (item >= nbig) break;
+        const uint32_t j = a.big_list[item];
+        if (tid == 0) {
+            const uint4 rr = philox4x32_10(make_uint4(0u, j, a.epoch, STREAM_ROOT), a.key0, a.key1);
+            const uint32_t root = __umulhi(rr.x, n);
+            hash_insert(H, HMASK, HSHIFT, root, a.ctr);
+            Q[0] = root;
+            QB[0] = __ldg(a.g.row_ptr + root);
+            QE[0] = __ldg(a.g.row_ptr + root + 1);
+            s.tail = 1;
+            s.overflow = 0;
+            s.fail = 0;
+        }
+        __syncthreads();
+
+        if (a.model == MODEL_IC) {
+            uint32_t head = 0;
+            for (;;) {
+                const uint32_t tail = s.tail;  // the previous level ended with a barrier
+                if (head >= tail || s.overflow) break;
+                for (uint32_t c0 = head; c0 < tail; c0 += BP_THREADS) {
+                    const uint32_t cnt = min((uint32_t)BP_THREADS, tail - c0);
+                    uint32_t b = 0, e = 0, ng = 0, gfirst = 0;
+                    if (tid < cnt) {
+                        b = QB[c0 + tid];
+                        e = QE[c0 + tid];
+                        if (e > b) {
+                            gfirst = b >> 2;
+                            ng = ((e - 1) >> 2) - gfirst + 1;
+                        }
+                    }
+                    uint32_t total;
+                    const uint32_t ex = block_excl_scan(ng, s.warp, total);
+                    s.scan[tid] = ex + ng;
+                    s.g0[tid] = gfirst;
+                    s.eb[tid] = b;
+                    s.ee[tid] = e;
+                    __syncthreads();
+                    for (uint32_t base = 0; base < total; base += BP_THREADS * BP_ILP) {
+                        // a set past BQ stops growing here: each warp inserts at most one
+                        // more round after it sees the flag, so the table stays under 2*BQ
+                        if (*(volatile int*)&s.overflow) break;
+                        uint32_t gg[BP_ILP], eb[BP_ILP], ee[BP_ILP];
+#pragma unroll
+                        for (int q = 0; q < BP_ILP; q++) {
+                            const uint32_t t = base + q * BP_THREADS + tid;
+                            gg[q] = 0;
+                            eb[q] = 0;
+                            ee[q] = 0;
+                            if (t < total) {
+                                uint32_t lo = 0, hi = cnt - 1;
+                                while (lo < hi) {
+                                    const uint32_t mid = (lo + hi) >> 1;
+                                    if (s.scan[mid] > t) hi = mid;
+                                    else lo = mid + 1;
+                                }
+                                gg[q] = s.g0[lo] + (t - (lo ? s.scan[lo - 1] : 0u));
+                                eb[q] = s.eb[lo];
+                                ee[q] = s.ee[lo];
+                            }
+                        }
+                        uint32_t m = 0;
+#pragma unroll
+                        for (int q = 0; q < BP_ILP; q++)
+                            if (ee[q] > eb[q]) m |= group_coins(a, j, gg[q], eb[q], ee[q], &set_scanned) << (4 * q);
+                        set_live += __popc(m);
+                        const uint32_t rounds = __reduce_max_sync(0xFFFFFFFFu, (uint32_t)__popc(m));
+                        for (uint32_t r = 0; r < rounds; r++) {
+                            if (*(volatile int*)&s.overflow) break;
+                            bool isnew = false;
+                            uint32_t u = 0;
+                            if (m) {
+                                const uint32_t bit = __ffs(m) - 1;
+                                m &= m - 1;
+                                uint32_t g = gg[0];
+#pragma unroll
+                                for (int q = 1; q < BP_ILP; q++)
+                                    if ((bit >> 2) == (uint32_t)q) g = gg[q];
+                                u = __ldg(a.g.col + g * 4u + (bit & 3u));
+                                isnew = hash_insert(H, HMASK, HSHIFT, u, a.ctr);
+                            }
+                            mid_append(a, s, Q, QB, QE, isnew, u);
+                        }
+                    }
+                    __syncthreads();
+                }
+                head = tail;
+            }
+        } else if (warp == 0) {
+            uint32_t v = Q[0], tail = 1;
+            for (;;) {
+                const uint32_t b = __ldg(a.g.row_ptr + v), e = __ldg(a.g.row_ptr + v + 1);
+                if (b == e) break;
+                const uint32_t x = philox4x32_10(make_uint4(v, j, a.epoch, STREAM_LT), a.key0, a.key1).x;
+                unsigned long long Qs = 0;
+                uint32_t chosen = NONE;
+                for (uint32_t base = b; base < e; base += 32) {
+                    const uint32_t idx = base + lane;
+                    const uint32_t qi = idx < e ? __ldg(a.g.q + idx) : 0u;
+                    const unsigned long long incl = warp_incl_scan_u64(qi) + Qs;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, idx < e && (unsigned long long)x < incl);
+                    if (bal) {
+                        chosen = base + __ffs(bal) - 1;
+                        break;
+                    }
+                    Qs = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                }
+                set_scanned += (chosen == NONE ? e - b : chosen - b + 1) * (lane == 0);
+                if (chosen == NONE) break;
+                set_live += (lane == 0);
+                const uint32_t u = __ldg(a.g.col + chosen);
+                uint32_t isnew = 0;
+                if (lane == 0) isnew = hash_insert(H, HMASK, HSHIFT, u, a.ctr);
+                isnew = __shfl_sync(0xFFFFFFFFu, isnew, 0);
+                if (!isnew) break;
+                if (tail >= BQ) {
+                    if (lane == 0) s.overflow = 1;
+                    break;
+                }
+                if (lane == 0) Q[tail] = u;
+                tail++;
+                v = u;
+            }
+            if (lane == 0) s.tail = tail;
+        }
+        __syncthreads();
+        const uint32_t size = min(s.tail, BQ);
+        const bool overflow = s.overflow != 0;
+
+        if (overflow) {
+            if (tid == 0) a.giant_list[atomicAdd(&a.ctr->giant_count, 1ull)] = j;
+        } else if (a.mode == MODE_HIST) {
+            if ((unsigned long long)a.cut * size <= n)
+                for (uint32_t i = tid; i < size; i += BP_THREADS) atomicAdd(&a.freq[Q[i]], 1u);
+        } else if (a.mode == MODE_RAW) {
+            if (tid == 0) {
+                s.item = 0;
+                const unsigned long long off = atomicAdd(&a.ctr->raw_cursor, (unsigned long long)size);
+                s.fail = off + size > a.raw_cap;
+                s.warp[0] = (uint32_t)off;
+                s.warp[1] = (uint32_t)(off >> 32);
+            }
+            __syncthreads();
+            const unsigned long long off = ((unsigned long long)s.warp[1] << 32) | s.warp[0];
+            if (!s.fail) {
+                for (uint32_t i = tid; i < size; i += BP_THREADS) a.raw_heap[off + i] = Q[i];
+                if (tid == 0) {
+                    a.recs[j] = make_rec(KIND_RAW, off, size, 0);
+                    atomicAdd(&a.ctr->sets_raw, 1ull);
+                    atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                    atomicAdd(&a.ctr->words_used, (unsigned long long)size);
+                }
+            }
+        } else if ((unsigned long long)a.cut * size > n) {
+            const unsigned long long row = (((unsigned long long)n + 31) / 32 + 3) & ~3ull;
+            if (tid == 0) {
+                const unsigned long long off = atomicAdd(&a.ctr->bm_cursor, row);
+                s.fail = off + row > a.bm_cap;
+                s.warp[0] = (uint32_t)off;
+                s.warp[1] = (uint32_t)(off >> 32);
+            }
+            __syncthreads();
+            const unsigned long long off = ((unsigned long long)s.warp[1] << 32) | s.warp[0];
+            if (!s.fail) {
+                for (uint32_t i = tid; i < size; i += BP_THREADS) {
+                    const uint32_t v = Q[i];
+                    atomicOr(&a.bm_heap[off + (v >> 5)], 1u << (v & 31));
+                }
+                if (tid == 0) {
+                    a.recs[j] = make_rec(KIND_BITMAP, off, size, 0);
+                    atomicAdd(&a.ctr->sets_bm, 1ull);
+                    atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                    atomicAdd(&a.ctr->words_used, row);
+                }
+            }
+        } else {
+            // keys (rank, or RAW_FLAG|id) sorted in shared memory, reusing QB
+            uint32_t P = 2;
+            while (P < size) P <<= 1;
+            for (uint32_t i = tid; i < P; i += BP_THREADS) {
+                uint32_t key = 0xFFFFFFFFu;
+                if (i < size) {
+                    const uint32_t v = Q[i];
+                    const uint32_t r = __ldg(a.cb.rank_of + v);
+                    key = (r != NONE) ? r : (RAW_FLAG | v);
+                }
+                QB[i] = key;
+            }
+            __syncthreads();
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (uint32_t i = tid; i < P; i += BP_THREADS) {
+                        const uint32_t ixj = i ^ jj;
+                        if (ixj > i) {
+                            const uint32_t x = QB[i], y = QB[ixj];
+                            if ((x > y) == ((i & k) == 0)) {
+                                QB[i] = y;
+                                QB[ixj] = x;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            if (warp == 0) {
+                WarpStats ws;
+                const bool ok = warp_huff_store(a, j, QB, size, s.stage, ws);
+                if (lane == 0) {
+                    s.fail = !ok;
+                    if (ok) {
+                        atomicAdd(&a.ctr->sets_huff, 1ull);
+                        atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                        atomicAdd(&a.ctr->code_bits, ws.bits);
+                        atomicAdd(&a.ctr->words_used, ws.words);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const bool failed = s.fail != 0;
+        if (tid == 0 && !overflow) {
+            if (failed) a.retry_list[atomicAdd(&a.ctr->retry_count, 1ull)] = j;
+            else atomicAdd(&a.ctr->sets_big, 1ull);
+        }
+        if (!overflow && !failed) {
+            scanned += set_scanned;
+            live += set_live;
+        }
+        for (uint32_t i = tid; i < BQ_HASH / 4; i += BP_THREADS) reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+    }
+    unsigned long long sc = scanned, lv = live;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        sc += __shfl_xor_sync(0xFFFFFFFFu, sc, d);
+        lv += __shfl_xor_sync(0xFFFFFFFFu, lv, d);
+    }
+    if (lane == 0) {
+        if (sc) atomicAdd(&a.ctr->edges_scanned, sc);
+        if (lv) atomicAdd(&a.ctr->edges_live, lv);
+    }
+}
+
+cudaError_t launch_sample_mid(const SampleArgs& a, uint32_t nbig, int sms, cudaStream_t s) {
+    if (nbig == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(sample_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)MID_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_mid_kernel, BP_THREADS, MID_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    uint32_t grid = (uint32_t)(sms * (per_sm > 0 ? per_sm : 1));
+    if (grid > nbig) grid = nbig;
+    sample_mid_kernel<<<grid, BP_THREADS, MID_DYN_SMEM, s>>>(a, nbig);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 template <uint32_t QW>

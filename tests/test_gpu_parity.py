@@ -166,17 +166,22 @@ def test_lt_sets(ctx, qw):
 
 
 def test_degenerate_graphs(ctx):
-    # p = 1 chain: every set is a prefix path (large sets use the block path)
-    P = 3000
-    g = synth.from_edges(P, [(i, i + 1) for i in range(P - 1)], prob=[1.0] * (P - 1))
+    # p = 1 chain (and LT weight 1): every set is a prefix path of up to 6000
+    # vertices, so sets go through the warp, shared-memory block (<= 4096) and
+    # global-bitmap block (> 4096) tiers
+    P = 6000
+    edges = [(i, i + 1) for i in range(P - 1)]
+    g = synth.from_edges(P, edges, prob=[1.0] * (P - 1), lt_weight=[1.0] * (P - 1))
     G = hbx.hbx_graph_create(ctx, g)
-    for enc in (0, 1):
-        p = hbx.hbx_pool_create(ctx, G, "IC", 5, opts(encode=enc, warmup_sets=50, warp_capacity=128))
-        hbx.hbx_pool_extend(ctx, p, 300)
-        op = oracle.Pool(g, oracle.IC, 5)
-        op.extend(300)
-        assert_same_sets(gpu_sets(ctx, p, 0, 300), oracle_sets(op, 0, 300))
-        hbx.hbx_pool_destroy(p)
+    for model, om in (("IC", oracle.IC), ("LT", oracle.LT)):
+        for enc in (0, 1):
+            p = hbx.hbx_pool_create(ctx, G, model, 5, opts(encode=enc, warmup_sets=50, warp_capacity=128))
+            hbx.hbx_pool_extend(ctx, p, 300)
+            op = oracle.Pool(g, om, 5)
+            op.extend(300)
+            assert_same_sets(gpu_sets(ctx, p, 0, 300), oracle_sets(op, 0, 300))
+            assert int(op.sizes().max()) > 4096
+            hbx.hbx_pool_destroy(p)
     hbx.hbx_graph_destroy(G)
     # no edges at all: every set is its root; greedy takes the most frequent roots
     g = synth.from_edges(50, [], prob=[])
