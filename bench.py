@@ -121,6 +121,24 @@ def oracle_sample_rate(g, w, target_s=15.0, budget_sets=None):
     return S / dt, S, cores, dt
 
 
+def replica_seed(rr_seed, rank):
+    """Philox key of rank `rank`'s replica: every rank solves its own instance."""
+    return rr_seed + 1000 * rank
+
+
+def reduce_over_ranks(total_ms, sets, device=None):
+    """(slowest rank's timed interval, sets summed over ranks) over the default
+    process group."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([total_ms, float(sets)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
+    sm = t.clone()
+    tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def run_reference(args, rank):
     import synth
     if rank != 0:
@@ -164,7 +182,7 @@ def run_hbx(args, rank, world, local_rank):
     hbx.build()
     w = synth.WORKLOADS[args.workload]
     g = w.graph()
-    seed = w.rr_seed + 1000 * rank
+    seed = replica_seed(w.rr_seed, rank)
     tc = hbx.torch_context(local_rank)
     ctx = tc.ctx
     G = hbx.hbx_graph_create(ctx, g)
@@ -198,12 +216,7 @@ def run_hbx(args, rank, world, local_rank):
     total_ms = sum(step_ms)
     sets = sum(s["theta"] for s in stats)
     if dist:
-        t = torch.tensor([total_ms, float(sets)], dtype=torch.float64, device=f"cuda:{local_rank}")
-        mx = t.clone()
-        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
-        sm = t.clone()
-        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
-        total_ms_all, sets_all = float(mx[0]), float(sm[1])
+        total_ms_all, sets_all = reduce_over_ranks(total_ms, sets, f"cuda:{local_rank}")
     else:
         total_ms_all, sets_all = total_ms, float(sets)
     value = sets_all / (total_ms_all / 1000.0)
@@ -228,6 +241,27 @@ def run_hbx(args, rank, world, local_rank):
             tdist.barrier()
         tc.close()
         return
+    # the plain one-launch-per-step form (int32 sets, block per set, selection
+    # launched round by round) on the same workload and seed, same timing rules
+    plain = None
+    if not args.no_plain and args.form == 1:
+        popts = hbx.hbx_default_options(encode=0, form=0)
+        hbx.hbx_imm(ctx, G, w.model, w.k, w.eps, w.ell, seed, popts)  # warm-up
+        pms, pr = [], None
+        for _ in range(args.steps):
+            with torch.cuda.stream(tc.stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record(tc.stream)
+            pr = hbx.hbx_imm(ctx, G, w.model, w.k, w.eps, w.ell, seed, popts)
+            ev1.record(tc.stream)
+            ev1.synchronize()
+            pms.append(ev0.elapsed_time(ev1))
+        pmean = sum(pms) / len(pms)
+        plain = {"ms_per_step": pmean, "value": pr["stats"]["theta"] / (pmean / 1000.0), "unit": UNIT,
+                 "encode": "int32", "batched_speedup": pmean / (total_ms / args.steps),
+                 "seeds_equal": bool(np.array_equal(pr["seeds"], r["seeds"])),
+                 "influence_equal": pr["influence"] == r["influence"]}
     # roofline of the dominant kernel (sampling fused with encoding)
     peak, peak_kind = peaks()
     alg_bytes = sum(8 * s["rr_vertices"] + 4 * s["edges_scanned"] + 4 * s["edges_live"] + s["pool_bytes"]
@@ -272,9 +306,10 @@ def run_hbx(args, rank, world, local_rank):
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "sample_warp_kernel + sample_block_kernel (fused encode)",
+                     "kernel": "sampler: warp, shared-memory block and HBM block kernels, encode fused",
                      "launches": klaunch, "kernel_s": ksec},
         "cpu_baseline": cpu,
+        "plain_form": plain,
         "clocks": clk,
     }
     print(json.dumps(out), flush=True)
@@ -308,6 +343,7 @@ def main():
     ap.add_argument("--form", type=int, default=1)
     ap.add_argument("--encode", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison leg")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -70,9 +70,12 @@ typedef struct {
     uint32_t warmup_sets;
     /* 0: sets stored uncompressed as 32-bit ids; 1: Huffman + bitmap. */
     uint32_t encode;
-    /* 0: plain form, one launch per step (one warp per set, no work stealing,
-     * selection launched step by step); 1: persistent work-stealing sampling
-     * fused with encoding, selection rounds replayed from a CUDA graph. */
+    /* 0: plain form, one launch per step: every set of a batch sampled by one
+     * thread block with HBM scratch, sets assigned to blocks statically, and
+     * the k selection rounds launched one by one with a host read-back after
+     * each; 1: persistent work-stealing warp kernel with shared-memory and
+     * HBM block tiers for the sets that outgrow it, fused with encoding, and
+     * the k selection rounds replayed from one CUDA graph. */
     uint32_t form;
     /* Philox counter word 2 of every draw; pools with different epochs are
      * independent.  Default 0. */

@@ -87,7 +87,12 @@ struct Counters {
     unsigned long long words_used;            // heap words held by emitted sets
     unsigned long long mid_work;              // work-stealing cursor of the shared-memory block kernel
     unsigned long long giant_count;           // sets too large for shared memory
-    unsigned long long pad[10];
+    // lowest offset of a heap allocation that did not fit (all ones: none); every
+    // allocation that fitted ends at or below it, so the host rolls the cursor back
+    unsigned long long raw_fail, code_fail, bm_fail;
+    // histogram passes: sets at or above the density cut, vertices of the others
+    unsigned long long hist_dense, hist_verts;
+    unsigned long long pad[5];
 };
 
 struct SampleArgs {
@@ -96,7 +101,8 @@ struct SampleArgs {
     uint32_t mode, cut;
     uint32_t j0, count;       // sets j0 .. j0+count-1, or list[0..count)
     const uint32_t* list;
-    uint32_t persistent;      // 1: work stealing over a fixed grid; 0: one warp per set
+    uint32_t persistent;      // 1: work stealing over a fixed grid; 0: the plain form
+    uint32_t direct;          // block kernel: sample the batch itself, statically assigned
     uint32_t group_budget;    // 4-edge groups a warp may scan for one set before handing it to a block
     uint32_t* freq;           // MODE_HIST: warm-up vertex frequencies [n]
     SetRec* recs;

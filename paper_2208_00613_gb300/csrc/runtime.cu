@@ -349,9 +349,9 @@ int grow_buffer(hbx_pool* p, void** buf, size_t old_bytes, size_t new_bytes, siz
 
 static const uint64_t HEAP_SLACK = 64;  // words past the end, for the decoder's look-ahead
 
-static int grow_heap(hbx_pool* p, Heap& h, uint64_t need_words) {
+static int grow_heap(hbx_pool* p, Heap& h, uint64_t need_words, bool exact = false) {
     if (need_words <= h.cap) return HBX_OK;
-    uint64_t nc = std::max<uint64_t>(need_words + need_words / 4, h.cap * 2);
+    uint64_t nc = exact ? need_words : std::max<uint64_t>(need_words + need_words / 4, h.cap * 2);
     nc = std::max<uint64_t>(nc, 1u << 16);
     nc = (nc + 3) & ~3ull;
     RC(grow_buffer(p, (void**)&h.d, h.d ? (h.cap + HEAP_SLACK) * 4 : 0, (nc + HEAP_SLACK) * 4, h.cap * 4));
@@ -418,6 +418,7 @@ static int reset_launch_counters(hbx_pool* p) {
     CK(cudaMemsetAsync(p->ctr, 0, 2 * sizeof(unsigned long long), p->stream));  // work, big_work
     CK(cudaMemsetAsync(&p->ctr->big_count, 0, 2 * sizeof(unsigned long long), p->stream));
     CK(cudaMemsetAsync(&p->ctr->mid_work, 0, 2 * sizeof(unsigned long long), p->stream));  // + giant_count
+    CK(cudaMemsetAsync(&p->ctr->raw_fail, 0xFF, 3 * sizeof(unsigned long long), p->stream));
     return HBX_OK;
 }
 
@@ -458,8 +459,49 @@ static SampleArgs sample_args(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t 
     return a;
 }
 
+// Time one sampler launch (unless it is a histogram pass) and read the counters.
+template <class F>
+static int timed_launch(hbx_pool* p, bool timed, F&& launch) {
+    hbx_ctx* ctx = p->ctx;
+    if (timed) CK(cudaEventRecord(p->ev0, p->stream));
+    CK(launch());
+    if (timed) CK(cudaEventRecord(p->ev1, p->stream));
+    p->launches++;
+    RC(read_counters(p));
+    if (timed) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        p->sample_kernel_s += ms * 1e-3;
+        p->sample_kernel_launches++;
+    }
+    return HBX_OK;
+}
+
+// Run the block kernel over `nitems` sets: the giant list, or with a.direct the
+// batch itself.  Each resident cluster holds one scratch slot (an n-bit visited
+// bitmap and an n-entry queue in HBM); the slots take at most 32 GB, or an
+// eighth of the pool's device-memory limit.
+static int run_block_path(hbx_pool* p, SampleArgs a, uint32_t nitems, uint32_t csize, bool timed) {
+    const uint64_t slot_bytes = p->bp_words * 12 + (uint64_t)p->g->n * 4;
+    uint64_t budget = 32ull << 30;
+    if (p->o.max_device_bytes) budget = std::min<uint64_t>(budget, p->o.max_device_bytes / 8);
+    const uint64_t mem_slots = std::max<uint64_t>(1, budget / slot_bytes);
+    uint32_t slots = std::min<uint32_t>(nitems, (uint32_t)block_path_max_clusters(csize));
+    slots = (uint32_t)std::min<uint64_t>(slots, std::max<uint64_t>(mem_slots, p->bp_slots));
+    RC(ensure_block_scratch(p, slots));
+    a.bp_visited = p->bp_visited;
+    a.bp_rbits = p->bp_rbits;
+    a.bp_queue = p->bp_queue;
+    a.bp_aux = p->bp_aux;
+    return timed_launch(p, timed, [&] { return launch_sample_block(a, nitems, slots, csize, p->stream); });
+}
+
 // Sample sets (range [j0, j0+count) or list) in `mode`, handling sets too large
 // for a warp and heaps that run out.  The list, if any, is a device array.
+// The batched form runs the persistent warp kernel, then the shared-memory
+// block kernel on the sets that outgrew a warp, then the HBM-scratch block
+// kernel on those that outgrew shared memory.  The plain form runs every set
+// of the batch through the HBM-scratch block kernel, one block per set.
 static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, const uint32_t* list,
                       uint32_t* freq, uint32_t cut, const Shape& sh) {
     hbx_ctx* ctx = p->ctx;
@@ -469,60 +511,31 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
         RC(reset_launch_counters(p));
         const bool timed = mode != MODE_HIST;
         SampleArgs a = sample_args(p, mode, j0, count, list, freq, cut, sh);
-        if (timed) CK(cudaEventRecord(p->ev0, p->stream));
-        CK(launch_sample_warp(a, sh.qw, ctx->sms, p->stream));
-        if (timed) CK(cudaEventRecord(p->ev1, p->stream));
-        p->launches++;
-        RC(read_counters(p));
-        if (timed) {
-            float ms = 0;
-            CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
-            p->sample_kernel_s += ms * 1e-3;
-            p->sample_kernel_launches++;
-        }
-        const uint32_t nmid = (uint32_t)p->hc.big_count;
-        if (nmid) {
-            // sets that outgrew a warp: one block each, held in shared memory
-            if (timed) CK(cudaEventRecord(p->ev0, p->stream));
-            CK(launch_sample_mid(a, nmid, ctx->sms, p->stream));
-            if (timed) CK(cudaEventRecord(p->ev1, p->stream));
-            p->launches++;
-            RC(read_counters(p));
-            if (timed) {
-                float ms = 0;
-                CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
-                p->sample_kernel_s += ms * 1e-3;
-                p->sample_kernel_launches++;
-            }
-        }
-        const uint32_t nbig = (uint32_t)p->hc.giant_count;
-        if (nbig) {
-            // sets that outgrew shared memory: one block or cluster each, with an
-            // n-bit visited bitmap and an n-entry queue in HBM (one scratch slot
-            // per resident cluster, at most 8 GB of slots)
-            const uint64_t slot_bytes = p->bp_words * 12 + (uint64_t)p->g->n * 4;
-            const uint64_t mem_slots = std::max<uint64_t>(1, (8ull << 30) / slot_bytes);
-            const uint32_t csize = sh.bc ? sh.bc : 1u;
-            uint32_t slots = std::min<uint32_t>(nbig, (uint32_t)block_path_max_clusters(csize));
-            slots = (uint32_t)std::min<uint64_t>(slots, std::max<uint64_t>(mem_slots, p->bp_slots));
-            RC(ensure_block_scratch(p, slots));
-            a = sample_args(p, mode, j0, count, list, freq, cut, sh);
-            a.big_list = p->giant_list;
-            if (timed) CK(cudaEventRecord(p->ev0, p->stream));
-            CK(launch_sample_block(a, nbig, slots, csize, p->stream));
-            if (timed) CK(cudaEventRecord(p->ev1, p->stream));
-            p->launches++;
-            RC(read_counters(p));
-            if (timed) {
-                float ms = 0;
-                CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
-                p->sample_kernel_s += ms * 1e-3;
-                p->sample_kernel_launches++;
+        if (!a.persistent) {
+            a.direct = 1;
+            RC(run_block_path(p, a, count, 1u, timed));
+        } else {
+            RC(timed_launch(p, timed, [&] { return launch_sample_warp(a, sh.qw, ctx->sms, p->stream); }));
+            const uint32_t nmid = (uint32_t)p->hc.big_count;
+            if (nmid) RC(timed_launch(p, timed, [&] { return launch_sample_mid(a, nmid, ctx->sms, p->stream); }));
+            const uint32_t nbig = (uint32_t)p->hc.giant_count;
+            if (nbig) {
+                SampleArgs b = a;
+                b.big_list = p->giant_list;
+                RC(run_block_path(p, b, nbig, sh.bc ? sh.bc : 1u, timed));
             }
         }
         const uint32_t nretry = (uint32_t)p->hc.retry_count;
         if (nretry == 0) break;
-        // grow whichever heap overflowed, then redo the listed sets
+        // Every allocation that fitted a heap lies below the lowest failed
+        // offset, and every one at or past it failed: the listed sets need
+        // exactly the words past it.  Roll each cursor back there, grow the
+        // heaps to the old cursor, and redo the listed sets.
+        const unsigned long long fails[3] = {p->hc.raw_fail, p->hc.code_fail, p->hc.bm_fail};
+        unsigned long long rolled[3] = {p->hc.raw_cursor, p->hc.code_cursor, p->hc.bm_cursor};
+        for (int h = 0; h < 3; h++)
+            if (fails[h] != ~0ull) rolled[h] = fails[h];
+        CK(cudaMemcpyAsync(&p->ctr->raw_cursor, rolled, sizeof(rolled), cudaMemcpyHostToDevice, p->stream));
         RC(grow_heap(p, p->raw, p->hc.raw_cursor + 1024));
         RC(grow_heap(p, p->code, p->hc.code_cursor + 1024));
         const uint64_t row = (((uint64_t)p->g->n + 31) / 32 + 3) & ~3ull;
@@ -677,6 +690,10 @@ static int build_codebook(hbx_pool* p, const std::vector<uint32_t>& freq) {
 // ---------------------------------------------------------------------------
 static int choose_shape(hbx_pool* p, Shape* out) {
     hbx_ctx* ctx = p->ctx;
+    if (!p->o.form) {  // the plain form runs the block kernel only
+        *out = {256, 2048, 1};
+        return HBX_OK;
+    }
     if (p->o.warp_capacity) {
         out->qw = p->o.warp_capacity;
         out->gb = p->o.warp_group_budget ? p->o.warp_group_budget : 2048u;
@@ -694,7 +711,6 @@ static int choose_shape(hbx_pool* p, Shape* out) {
     }
     const Shape cands[] = {{64, 0, 1},      {128, 256, 1},  {128, 1024, 1}, {256, 4096, 1},
                            {128, 1024, 2},  {256, 1024, 2}, {256, 4096, 4}, {512, 4096, 1}};
-    const uint32_t ncal = 8192;
     uint32_t* freq = nullptr;
     RC(grow_buffer(p, (void**)&freq, 0, (size_t)p->g->n * 4, 0));
     cudaEvent_t e0, e1;
@@ -704,7 +720,25 @@ static int choose_shape(hbx_pool* p, Shape* out) {
     Shape best = {256, 2048, 1};
     const uint32_t base = 0x40000000u;  // calibration ids, never part of a pool prefix
     const unsigned long long sc0 = p->hc.edges_scanned, lv0 = p->hc.edges_live;
-    for (int rep = 0; rep < 2; rep++) {
+    // Calibration batch: 8192 sets timed twice per shape, or, where a probe of
+    // 256 sets shows heavy sets, as many as scan about 2^31 edges, timed once.
+    uint32_t ncal = 8192;
+    int reps = 2;
+    {
+        const uint32_t nprobe = 256;
+        int r = run_sample(p, MODE_HIST, base + 0x20000000u, nprobe, nullptr, freq, 0u, cands[0]);
+        if (r) {
+            dfree(ctx, freq);
+            return r;
+        }
+        const double per_set = (double)(p->hc.edges_scanned - sc0) / nprobe;
+        const double budget = 2147483648.0;
+        if (per_set * ncal > budget) {
+            ncal = std::max<uint32_t>(64, (uint32_t)(budget / per_set) & ~63u);
+            reps = 1;
+        }
+    }
+    for (int rep = 2 - reps; rep < 2; rep++) {
         for (const Shape& sh : cands) {
             CK(cudaEventRecord(e0, p->stream));
             int r = run_sample(p, MODE_HIST, base, ncal, nullptr, freq, 0u, sh);
@@ -751,9 +785,13 @@ static int ensure_codebook(hbx_pool* p) {
     const uint32_t n = p->g->n;
     RC(grow_buffer(p, (void**)&freq, 0, (size_t)n * 4, 0));
     const unsigned long long sc0 = p->hc.edges_scanned, lv0 = p->hc.edges_live;
+    const unsigned long long hd0 = p->hc.hist_dense, hv0 = p->hc.hist_verts;
     int r = run_sample(p, MODE_HIST, 0, (uint32_t)p->W, nullptr, freq, p->o.density_cut, p->shape);
     p->aux_scanned += p->hc.edges_scanned - sc0;
     p->aux_live += p->hc.edges_live - lv0;
+    p->hist_sets = p->W;
+    p->hist_dense = p->hc.hist_dense - hd0;
+    p->hist_verts = p->hc.hist_verts - hv0;
     std::vector<uint32_t> hf(n);
     if (!r) {
         cudaError_t e = cudaMemcpyAsync(hf.data(), freq, (size_t)n * 4, cudaMemcpyDeviceToHost, p->stream);
@@ -764,6 +802,39 @@ static int ensure_codebook(hbx_pool* p) {
     p->device_bytes -= (size_t)n * 4;
     if (r) return r;
     return build_codebook(p, hf);
+}
+
+// Grow the heaps ahead of a batch of `count` sets by projecting each heap's
+// words per set from the sets stored so far or, before the first batch of an
+// encoded pool, from the warm-up pass (sizes of the same first sets, with the
+// frequency-weighted mean code length).  Heavy sets then seldom overflow a
+// heap, which would make them be sampled twice.
+static int reserve_heaps(hbx_pool* p, uint64_t count) {
+    const uint64_t row = (((uint64_t)p->g->n + 31) / 32 + 3) & ~3ull;
+    double per[3] = {0, 0, 0}, dense = 0;  // raw, code, bitmap words per set; dense fraction
+    if (p->T) {
+        per[0] = (double)p->hc.raw_cursor / (double)p->T;
+        per[1] = (double)p->hc.code_cursor / (double)p->T;
+        dense = (double)p->hc.sets_bm / (double)p->T;
+    } else if (p->hist_sets && p->has_cb) {
+        double fl = 0, f = 0;
+        for (uint32_t v = 0; v < p->g->n; v++) {
+            fl += (double)p->h_freq[v] * p->h_len[v];
+            f += (double)p->h_freq[v];
+        }
+        const double bits = f > 0 ? fl / f : 32.0;
+        per[1] = (double)p->hist_verts / (double)p->hist_sets * (bits + 2.0) / 32.0 + 2.0;
+        dense = (double)p->hist_dense / (double)p->hist_sets;
+    } else {
+        return HBX_OK;
+    }
+    // the dense count of a batch varies like a binomial: three deviations of room
+    const double c = (double)count;
+    const double nd = c * dense + 3.0 * std::sqrt(c * dense * (1.0 - dense)) + 1.0;
+    RC(grow_heap(p, p->raw, p->hc.raw_cursor + (uint64_t)(per[0] * c * 1.1) + 1024, true));
+    RC(grow_heap(p, p->code, p->hc.code_cursor + (uint64_t)(per[1] * c * 1.1) + 1024, true));
+    if (dense > 0) RC(grow_heap(p, p->bm, p->hc.bm_cursor + (uint64_t)nd * row, true));
+    return HBX_OK;
 }
 
 int pool_extend(hbx_pool* p, uint64_t T) {
@@ -781,6 +852,7 @@ int pool_extend(hbx_pool* p, uint64_t T) {
         const uint64_t j0 = p->T;
         const uint32_t count = (uint32_t)std::min<uint64_t>(T - j0, batch_max);
         const unsigned long long verts_before = p->hc.rr_vertices;
+        RC(reserve_heaps(p, count));
         RC(run_sample(p, mode, (uint32_t)j0, count, nullptr, nullptr, p->o.density_cut, p->shape));
         // selection index of the new sets
         const uint64_t added = p->hc.rr_vertices - verts_before;
@@ -1128,8 +1200,9 @@ int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds
         const uint64_t T1 = (uint64_t)std::ceil(b.lambda_p / (dn / std::ldexp(1.0, 1)));
         p->W = (T1 + 7) / 8;
     }
-    std::vector<uint32_t> tmp(k);
-    uint64_t Ti = 0;
+    std::vector<uint32_t> last_seeds(k);
+    std::vector<uint64_t> last_marg(k);
+    uint64_t Ti = 0, last_T = 0, last_cov = 0;
     double LB = 1.0;
     uint32_t rounds = 0;
     const uint32_t imax = ilog2_floor(n) - 1;
@@ -1139,7 +1212,12 @@ int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds
         if (t > Ti) Ti = t;
         RC(pool_extend(p, Ti));
         uint64_t cov = 0;
-        RC(pool_select(p, Ti, k, tmp.data(), nullptr, &cov));
+        if (Ti != last_T) {
+            RC(pool_select(p, Ti, k, last_seeds.data(), last_marg.data(), &cov));
+            last_T = Ti;
+            last_cov = cov;
+        }
+        cov = last_cov;
         rounds++;
         const double est = dn * (double)cov / (double)Ti;
         if (est >= (1.0 + b.epsp) * x) {
@@ -1151,7 +1229,16 @@ int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds
     if (T < Ti) T = Ti;
     RC(pool_extend(p, T));
     uint64_t cov = 0;
-    RC(pool_select(p, T, k, seeds, marginal, &cov));
+    if (T == last_T) {
+        // greedy selection is a function of the sets [0, T): the last round's
+        // result is the final one
+        for (uint32_t i = 0; i < k; i++) seeds[i] = last_seeds[i];
+        if (marginal)
+            for (uint32_t i = 0; i < k; i++) marginal[i] = last_marg[i];
+        cov = last_cov;
+    } else {
+        RC(pool_select(p, T, k, seeds, marginal, &cov));
+    }
     *influence = dn * (double)cov / (double)T;
     if (stats) {
         fill_stats(p, stats);

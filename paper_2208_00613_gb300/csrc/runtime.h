@@ -76,6 +76,7 @@ struct hbx_pool {
     hbx::Counters hc{};
     double* moments = nullptr;
     unsigned long long aux_scanned = 0, aux_live = 0;  // edges of warm-up/calibration passes
+    uint64_t hist_sets = 0, hist_dense = 0, hist_verts = 0;  // warm-up pass: sets, dense sets, other vertices
     // codebook
     bool has_cb = false;
     uint64_t W = 0;

@@ -279,7 +279,10 @@ __device__ bool warp_huff_store(const SampleArgs& a, uint32_t j, const uint32_t*
     unsigned long long off = 0;
     if (lane == 0) off = words ? atomicAdd(&a.ctr->code_cursor, words) : 0ull;
     off = __shfl_sync(0xFFFFFFFFu, off, 0);
-    if (off + words > a.code_cap) return false;
+    if (off + words > a.code_cap) {
+        if (lane == 0) atomicMin(&a.ctr->code_fail, off);
+        return false;
+    }
 
     // pack 32 codes at a time into the stage, write completed words
     uint32_t* out = a.code_heap + off + nside + n_raw;
@@ -343,15 +346,23 @@ __device__ bool warp_emit(const SampleArgs& a, uint32_t j, uint32_t* queue, uint
     const uint32_t lane = lane_id();
     const uint32_t n = a.g.n;
     if (a.mode == MODE_HIST) {
-        if ((unsigned long long)a.cut * size <= n)
+        const bool dense = (unsigned long long)a.cut * size > n;
+        if (!dense)
             for (uint32_t i = lane; i < size; i += 32) atomicAdd(&a.freq[queue[i]], 1u);
+        if (lane == 0) {  // sizes of the sampled sets, kept apart from the pool's statistics
+            st.bm += dense;
+            st.verts += dense ? 0u : size;
+        }
         return true;
     }
     if (a.mode == MODE_RAW) {
         unsigned long long off = 0;
         if (lane == 0) off = atomicAdd(&a.ctr->raw_cursor, (unsigned long long)size);
         off = __shfl_sync(0xFFFFFFFFu, off, 0);
-        if (off + size > a.raw_cap) return false;
+        if (off + size > a.raw_cap) {
+            if (lane == 0) atomicMin(&a.ctr->raw_fail, off);
+            return false;
+        }
         for (uint32_t i = lane; i < size; i += 32) a.raw_heap[off + i] = queue[i];
         if (lane == 0) {
             a.recs[j] = make_rec(KIND_RAW, off, size, 0);
@@ -367,7 +378,10 @@ __device__ bool warp_emit(const SampleArgs& a, uint32_t j, uint32_t* queue, uint
         unsigned long long off = 0;
         if (lane == 0) off = atomicAdd(&a.ctr->bm_cursor, row);
         off = __shfl_sync(0xFFFFFFFFu, off, 0);
-        if (off + row > a.bm_cap) return false;
+        if (off + row > a.bm_cap) {
+            if (lane == 0) atomicMin(&a.ctr->bm_fail, off);
+            return false;
+        }
         for (uint32_t i = lane; i < size; i += 32) {
             const uint32_t v = queue[i];
             atomicOr(&a.bm_heap[off + (v >> 5)], 1u << (v & 31));
@@ -415,13 +429,8 @@ __global__ void __launch_bounds__(WP_WARPS * 32) sample_warp_kernel(SampleArgs a
     WarpStats st;
 
     uint32_t item = 0, item_end = 0;
-    if (!a.persistent) {
-        item = blockIdx.x * WP_WARPS + warp;
-        item_end = min(item + 1, a.count);
-    }
     for (;;) {
         if (item >= item_end) {
-            if (!a.persistent) break;
             unsigned long long b = 0;
             if (lane == 0) b = atomicAdd(&a.ctr->work, (unsigned long long)WORK_CHUNK);
             b = __shfl_sync(0xFFFFFFFFu, b, 0);
@@ -456,10 +465,10 @@ __global__ void __launch_bounds__(WP_WARPS * 32) sample_warp_kernel(SampleArgs a
     if (lane == 0) {
         if (sc) atomicAdd(&a.ctr->edges_scanned, sc);
         if (lv) atomicAdd(&a.ctr->edges_live, lv);
-        if (st.verts) atomicAdd(&a.ctr->rr_vertices, st.verts);
+        if (st.verts) atomicAdd(a.mode == MODE_HIST ? &a.ctr->hist_verts : &a.ctr->rr_vertices, st.verts);
         if (st.bits) atomicAdd(&a.ctr->code_bits, st.bits);
         if (st.huff) atomicAdd(&a.ctr->sets_huff, st.huff);
-        if (st.bm) atomicAdd(&a.ctr->sets_bm, st.bm);
+        if (st.bm) atomicAdd(a.mode == MODE_HIST ? &a.ctr->hist_dense : &a.ctr->sets_bm, st.bm);
         if (st.raw) atomicAdd(&a.ctr->sets_raw, st.raw);
         if (st.words) atomicAdd(&a.ctr->words_used, st.words);
     }
@@ -517,6 +526,8 @@ __device__ uint32_t compact_bits(uint32_t* words, uint64_t nwords, uint32_t* out
 }
 
 constexpr uint32_t BP_SORT_MAX = 4096;  // sets up to this size are sorted in shared memory
+constexpr uint32_t BP_LIVE = 4096;      // live edges staged per pass (in the sort buffer)
+static_assert(BP_LIVE <= BP_SORT_MAX && BP_LIVE % BP_THREADS == 0, "live stage");
 
 struct BlockShared {
     uint32_t keys[BP_SORT_MAX];
@@ -596,30 +607,51 @@ __device__ uint32_t block_bfs_ic(const SampleArgs& a, uint32_t j, uint32_t* visi
                 for (int q = 0; q < BP_ILP; q++)
                     if (ok[q]) m |= group_coins(a, j, gg[q], eb[q], ee[q], scanned) << (4 * q);
                 *live += __popc(m);
-                // insert live edges one per lane per round (rare under most models)
-                uint32_t rounds = __reduce_max_sync(0xFFFFFFFFu, (uint32_t)__popc(m));
-                for (uint32_t r = 0; r < rounds; r++) {
-                    bool isnew = false;
-                    uint32_t u = 0;
-                    if (m) {
-                        const uint32_t b = __ffs(m) - 1;
-                        m &= m - 1;
-                        uint32_t g = gg[0];
+                // Stage the step's live edges in shared memory, then take them one
+                // per thread, so that the col loads and visited updates of the
+                // whole block are in flight together.
+                uint32_t nlive;
+                const uint32_t first = block_excl_scan((uint32_t)__popc(m), s.warp, nlive);
+                for (uint32_t p0 = 0; p0 < nlive; p0 += BP_LIVE) {
+                    uint32_t idx = first, mm = m;
+                    while (mm) {
+                        const uint32_t b = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        if (idx >= p0 && idx < p0 + BP_LIVE) {
+                            uint32_t g = gg[0];
 #pragma unroll
-                        for (int q = 1; q < BP_ILP; q++)
-                            if ((b >> 2) == (uint32_t)q) g = gg[q];
-                        u = __ldg(a.g.col + g * 4u + (b & 3u));
-                        const uint32_t bit = 1u << (u & 31);
-                        isnew = !(atomicOr(&visited[u >> 5], bit) & bit);
+                            for (int q = 1; q < BP_ILP; q++)
+                                if ((b >> 2) == (uint32_t)q) g = gg[q];
+                            s.keys[idx - p0] = g * 4u + (b & 3u);
+                        }
+                        idx++;
                     }
-                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isnew);
-                    if (bal) {
-                        const uint32_t leader = __ffs(bal) - 1;
-                        uint32_t pos = 0;
-                        if (lane == leader) pos = atomicAdd(tail0, (uint32_t)__popc(bal));
-                        pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-                        if (isnew) queue[pos + __popc(bal & lanemask_lt())] = u;
+                    __syncthreads();
+                    const uint32_t nstage = min((uint32_t)BP_LIVE, nlive - p0);
+                    constexpr int PER = BP_LIVE / BP_THREADS;
+                    uint32_t u[PER];
+#pragma unroll
+                    for (int r = 0; r < PER; r++) {
+                        const uint32_t i = tid + r * BP_THREADS;
+                        u[r] = i < nstage ? __ldg(a.g.col + s.keys[i]) : NONE;
                     }
+                    uint32_t fresh = 0;  // bit r: u[r] was not yet visited
+#pragma unroll
+                    for (int r = 0; r < PER; r++) {
+                        if (u[r] != NONE) {
+                            const uint32_t bit = 1u << (u[r] & 31);
+                            if (!(atomicOr(&visited[u[r] >> 5], bit) & bit)) fresh |= 1u << r;
+                        }
+                    }
+                    const uint32_t c = __popc(fresh);
+                    const uint32_t incl = warp_incl_scan(c);
+                    uint32_t pos = 0;
+                    if (lane == 31 && incl) pos = atomicAdd(tail0, incl);
+                    pos = __shfl_sync(0xFFFFFFFFu, pos, 31) + incl - c;
+#pragma unroll
+                    for (int r = 0; r < PER; r++)
+                        if (fresh >> r & 1u) queue[pos++] = u[r];
+                    __syncthreads();  // the stage is free again
                 }
             }
             __syncthreads();
@@ -692,13 +724,19 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
     uint32_t* queue = a.bp_queue + (uint64_t)slot * n;
     unsigned long long scanned = 0, live = 0;  // emitted sets only
 
-    for (;;) {
+    const uint64_t nslots = gridDim.x / csize;
+    for (uint64_t round = 0;; round++) {
         unsigned long long set_scanned = 0, set_live = 0;
-        if (crank == 0 && tid == 0) s.item = (uint32_t)min(atomicAdd(&a.ctr->big_work, 1ull), (unsigned long long)nbig);
+        if (crank == 0 && tid == 0) {
+            // plain form: item i of the batch goes to slot i mod slots; otherwise
+            // the listed heavy sets are taken by work stealing
+            const unsigned long long next = a.direct ? slot + round * nslots : atomicAdd(&a.ctr->big_work, 1ull);
+            s.item = (uint32_t)min(next, (unsigned long long)nbig);
+        }
         cl.sync();
         const uint32_t item = *item0;
         if (item >= nbig) break;
-        const uint32_t j = a.big_list[item];
+        const uint32_t j = !a.direct ? a.big_list[item] : (a.list ? a.list[item] : a.j0 + item);
         if (crank == 0 && tid == 0) {
             const uint4 rr = philox4x32_10(make_uint4(0u, j, a.epoch, STREAM_ROOT), a.key0, a.key1);
             const uint32_t root = __umulhi(rr.x, n);
@@ -721,12 +759,17 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
         // ---- emit ----
         bool clear_by_list = true;
         if (a.mode == MODE_HIST) {
-            if ((unsigned long long)a.cut * size <= n)
+            if ((unsigned long long)a.cut * size <= n) {
                 for (uint32_t i = tid; i < size; i += BP_THREADS) atomicAdd(&a.freq[queue[i]], 1u);
+                if (tid == 0) atomicAdd(&a.ctr->hist_verts, (unsigned long long)size);
+            } else if (tid == 0) {
+                atomicAdd(&a.ctr->hist_dense, 1ull);
+            }
         } else if (a.mode == MODE_RAW) {
             if (tid == 0) {
                 s.off = atomicAdd(&a.ctr->raw_cursor, (unsigned long long)size);
                 s.fail = s.off + size > a.raw_cap;
+                if (s.fail) atomicMin(&a.ctr->raw_fail, s.off);
             }
             __syncthreads();
             if (!s.fail) {
@@ -743,6 +786,7 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
             if (tid == 0) {
                 s.off = atomicAdd(&a.ctr->bm_cursor, (unsigned long long)row);
                 s.fail = s.off + row > a.bm_cap;
+                if (s.fail) atomicMin(&a.ctr->bm_fail, s.off);
             }
             __syncthreads();
             uint4* vis4 = reinterpret_cast<uint4*>(visited);
@@ -850,6 +894,7 @@ __global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, 
             if (tid == 0) {
                 s.off = words ? atomicAdd(&a.ctr->code_cursor, words) : 0ull;
                 s.fail = s.off + words > a.code_cap;
+                if (s.fail) atomicMin(&a.ctr->code_fail, s.off);
             }
             __syncthreads();
             if (!s.fail) {
@@ -1111,13 +1156,18 @@ __global__ void __launch_bounds__(BP_THREADS) sample_mid_kernel(SampleArgs a, ui
         if (overflow) {
             if (tid == 0) a.giant_list[atomicAdd(&a.ctr->giant_count, 1ull)] = j;
         } else if (a.mode == MODE_HIST) {
-            if ((unsigned long long)a.cut * size <= n)
+            if ((unsigned long long)a.cut * size <= n) {
                 for (uint32_t i = tid; i < size; i += BP_THREADS) atomicAdd(&a.freq[Q[i]], 1u);
+                if (tid == 0) atomicAdd(&a.ctr->hist_verts, (unsigned long long)size);
+            } else if (tid == 0) {
+                atomicAdd(&a.ctr->hist_dense, 1ull);
+            }
         } else if (a.mode == MODE_RAW) {
             if (tid == 0) {
                 s.item = 0;
                 const unsigned long long off = atomicAdd(&a.ctr->raw_cursor, (unsigned long long)size);
                 s.fail = off + size > a.raw_cap;
+                if (s.fail) atomicMin(&a.ctr->raw_fail, off);
                 s.warp[0] = (uint32_t)off;
                 s.warp[1] = (uint32_t)(off >> 32);
             }
@@ -1137,6 +1187,7 @@ __global__ void __launch_bounds__(BP_THREADS) sample_mid_kernel(SampleArgs a, ui
             if (tid == 0) {
                 const unsigned long long off = atomicAdd(&a.ctr->bm_cursor, row);
                 s.fail = off + row > a.bm_cap;
+                if (s.fail) atomicMin(&a.ctr->bm_fail, off);
                 s.warp[0] = (uint32_t)off;
                 s.warp[1] = (uint32_t)(off >> 32);
             }
@@ -1245,16 +1296,10 @@ static cudaError_t launch_warp_t(const SampleArgs& a, int sms, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(sample_warp_kernel<QW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    uint32_t grid;
-    if (a.persistent) {
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_warp_kernel<QW>, WP_WARPS * 32, smem);
-        if (e != cudaSuccess) return e;
-        grid = (uint32_t)(sms * (per_sm > 0 ? per_sm : 1));
-    } else {
-        grid = (a.count + WP_WARPS - 1) / WP_WARPS;
-    }
-    if (grid == 0) return cudaSuccess;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_warp_kernel<QW>, WP_WARPS * 32, smem);
+    if (e != cudaSuccess) return e;
+    const uint32_t grid = (uint32_t)(sms * (per_sm > 0 ? per_sm : 1));
     sample_warp_kernel<QW><<<grid, WP_WARPS * 32, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -141,40 +141,100 @@ __global__ void __launch_bounds__(COUNT_THREADS) count_items_kernel(SelArgs a, c
     }
 }
 
-// Per-vertex sums over bitmap rows: thread (word w, batch b) adds word w of
-// each listed set in its batch into 8 bit-planes (a ripple-carry adder per bit
-// position), then adds sign * count to cnt[32w + bit].
-__global__ void bitmap_count_kernel(SelArgs a, const uint32_t* list, const uint32_t* list_len_dev,
-                                    uint32_t list_len_host, int sign) {
+// Carry-save adder: the bitwise sum of a, b, c is sum + 2 * carry.
+__device__ __forceinline__ void csa(uint32_t& carry, uint32_t& sum, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    carry = (a & b) | (u & c);
+    sum = u ^ c;
+}
+
+// Bit-sliced counter of up to 255 rows for the 32 bits of one word: planes of
+// weight 1, 2, 4 and 8, 16, 32, 64, 128 (Harley-Seal: eight rows pass through a
+// tree of seven carry-save adders, and only the weight-8 carry ripples on).
+struct Planes {
+    uint32_t ones = 0, twos = 0, fours = 0, h[5] = {0, 0, 0, 0, 0};
+    __device__ __forceinline__ void add8(const uint32_t* w) {
+        uint32_t twosA, twosB, foursA, foursB, eights;
+        csa(twosA, ones, ones, w[0], w[1]);
+        csa(twosB, ones, ones, w[2], w[3]);
+        csa(foursA, twos, twos, twosA, twosB);
+        csa(twosA, ones, ones, w[4], w[5]);
+        csa(twosB, ones, ones, w[6], w[7]);
+        csa(foursB, twos, twos, twosA, twosB);
+        csa(eights, fours, fours, foursA, foursB);
+        uint32_t c = eights;
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            const uint32_t t = h[i] & c;
+            h[i] ^= c;
+            c = t;
+        }
+    }
+    __device__ __forceinline__ uint32_t any() const { return ones | twos | fours | h[0] | h[1] | h[2] | h[3] | h[4]; }
+    __device__ __forceinline__ uint32_t count(uint32_t bit) const {
+        uint32_t hi = 0;
+#pragma unroll
+        for (int i = 4; i >= 0; i--) hi = (hi << 1) | ((h[i] >> bit) & 1u);
+        return ((ones >> bit) & 1u) + 2u * ((twos >> bit) & 1u) + 4u * ((fours >> bit) & 1u) + 8u * hi;
+    }
+};
+
+// Per-vertex sums over bitmap rows.  A tile is (batch of up to 255 listed sets,
+// blockDim.x x 4 consecutive words): the block stages the batch's row offsets
+// in shared memory, each thread streams its 16 bytes of every row (eight rows
+// in flight) into bit-sliced counters, then adds sign * count to cnt[32w + bit]
+// for every bit with a nonzero count.  Rows are padded to a multiple of 4 words
+// and 16-byte aligned.
+__global__ void __launch_bounds__(SEL_THREADS) bitmap_count_kernel(SelArgs a, const uint32_t* list,
+                                                                  const uint32_t* list_len_dev,
+                                                                  uint32_t list_len_host, int sign) {
+    __shared__ unsigned long long s_off[BM_BATCH];
+    __shared__ uint32_t s_n;
     const uint32_t nw = (a.n + 31) / 32;
+    const uint32_t nq = (nw + 3) / 4;  // 16-byte quads per row
     const uint32_t len = list_len_dev ? *list_len_dev : list_len_host;
     const uint32_t nbatch = (len + BM_BATCH - 1) / BM_BATCH;
-    const uint64_t total = (uint64_t)nw * nbatch;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t w = (uint32_t)(t % nw), b = (uint32_t)(t / nw);
+    const uint32_t nchunk = (nq + blockDim.x - 1) / blockDim.x;
+    const uint64_t tiles = (uint64_t)nbatch * nchunk;
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint32_t b = (uint32_t)(tile / nchunk), ch = (uint32_t)(tile % nchunk);
+        __syncthreads();  // the previous tile is done with s_off
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
         const uint32_t s0 = b * BM_BATCH, s1 = min(len, s0 + BM_BATCH);
-        uint32_t p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (uint32_t s = s0; s < s1; s++) {
-            const uint32_t j = list[s];
-            if (j >= a.T) continue;
-            uint32_t c = __ldg(a.bm_heap + rec_off(a.recs[j]) + w);
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const uint32_t t2 = p[i] & c;
-                p[i] ^= c;
-                c = t2;
-            }
+        for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+            const uint32_t j = list[i];
+            if (j < a.T) s_off[atomicAdd(&s_n, 1u)] = rec_off(a.recs[j]);
         }
-        const uint32_t any = p[0] | p[1] | p[2] | p[3] | p[4] | p[5] | p[6] | p[7];
-        if (!any) continue;
-        for (uint32_t bit = 0; bit < 32; bit++) {
-            if (!(any >> bit & 1u)) continue;
-            uint32_t c = 0;
+        __syncthreads();
+        const uint32_t rows = s_n;
+        const uint32_t q = ch * blockDim.x + threadIdx.x;
+        if (q >= nq) continue;
+        Planes pl[4];
+        for (uint32_t r0 = 0; r0 < rows; r0 += 8) {
+            uint32_t w[4][8];
 #pragma unroll
-            for (int i = 0; i < 8; i++) c |= ((p[i] >> bit) & 1u) << i;
-            const uint32_t v = w * 32 + bit;
-            if (c && v < a.n) atomicAdd(&a.cnt[v], sign * (int)c);
+            for (int r = 0; r < 8; r++) {
+                uint4 x = make_uint4(0, 0, 0, 0);
+                if (r0 + r < rows) x = __ldg(reinterpret_cast<const uint4*>(a.bm_heap + s_off[r0 + r]) + q);
+                w[0][r] = x.x;
+                w[1][r] = x.y;
+                w[2][r] = x.z;
+                w[3][r] = x.w;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) pl[c].add8(w[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            uint32_t any = pl[c].any();
+            const uint32_t wbase = (q * 4 + c) * 32;
+            while (any) {
+                const uint32_t bit = __ffs(any) - 1;
+                any &= any - 1;
+                const uint32_t v = wbase + bit;
+                if (v < a.n) atomicAdd(&a.cnt[v], sign * (int)pl[c].count(bit));
+            }
         }
     }
 }

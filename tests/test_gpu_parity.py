@@ -129,6 +129,25 @@ def test_encoded_sets_ic_tiny(ctx, qw, cut):
     hbx.hbx_graph_destroy(G)
 
 
+def test_encoded_sets_plain_form(ctx):
+    # the plain form samples and encodes every set with the HBM-scratch block kernel
+    w = synth.WORKLOADS["ic_rmat4k"]
+    g = workload_graph("ic_rmat4k")
+    G = hbx.hbx_graph_create(ctx, g)
+    T, W, cut = 2500, 300, 32
+    p = hbx.hbx_pool_create(ctx, G, "IC", w.rr_seed, opts(encode=1, warmup_sets=W, density_cut=cut, form=0))
+    hbx.hbx_pool_extend(ctx, p, T)
+    op = oracle.Pool(g, oracle.IC, w.rr_seed)
+    op.extend(T)
+    _check_encoded(ctx, p, op, g, W, cut, T)
+    st = hbx.hbx_pool_stats(ctx, p)
+    assert st["sets_big"] == T
+    sc, lv = op.edge_counts()
+    assert st["edges_scanned"] == sc and st["edges_live"] == lv
+    hbx.hbx_pool_destroy(p)
+    hbx.hbx_graph_destroy(G)
+
+
 def test_encoded_sets_wc_1m(ctx):
     """Weighted cascade on the 2^20-vertex graph: Huffman and bitmap sets, every
     set checked byte for byte on a prefix, decoded sets compared on the rest."""
