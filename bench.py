@@ -121,6 +121,20 @@ def oracle_sample_rate(g, w, target_s=15.0, budget_sets=None):
     return S / dt, S, cores, dt
 
 
+def count_roofline(stats, peak):
+    """Achieved bandwidth of the selections' count passes (decoding or
+    bit-plane summing every counted set once): bytes they read over their
+    CUDA-event time."""
+    cs = sum(s["count_kernel_s"] for s in stats)
+    cb = sum(s["count_bytes"] for s in stats)
+    if cs <= 0:
+        return None
+    ach = cb / cs / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "bytes_per_step": cb / len(stats), "kernel_s_per_step": cs / len(stats),
+            "kernel": "count_items_kernel + bitmap_count_kernel (+ count_raw_kernel)"}
+
+
 def replica_seed(rr_seed, rank):
     """Philox key of rank `rank`'s replica: every rank solves its own instance."""
     return rr_seed + 1000 * rank
@@ -137,6 +151,51 @@ def reduce_over_ranks(total_ms, sets, device=None):
     sm = t.clone()
     tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
     return float(mx[0]), float(sm[1])
+
+
+def serving_leg(hbx, synth, tc, resident, count, rate=20.0, seed=3):
+    """Poisson stream of IM queries over three resident graphs (the shapes of
+    ic_rmat4k, wc_rmat1m and lt_rmat4m, each carrying IC probabilities and LT
+    weights), model IC or LT, k in [10, 200], eps in {0.13, 0.2, 0.3, 0.5},
+    served with continuous batching; RR pools stay resident across queries."""
+    import numpy as np
+    handles = []
+    for name in ("ic_rmat4k", "wc_rmat1m", "lt_rmat4m"):
+        w = synth.WORKLOADS[name]
+        g = resident.get(name) or w.graph()
+        if g.lt_weight is None:
+            g.lt_weight = synth.lt_weights(g, w.graph_seed)
+        if g.prob is None:
+            g.prob = synth.ic_uniform(g, w.graph_seed, 0.1)
+        handles.append(hbx.hbx_graph_create(tc.ctx, g))
+    qs = synth.poisson_queries(seed=seed, count=count, rate_per_s=rate, graphs=[0, 1, 2])
+    srv = hbx.hbx_server_create(tc.ctx, 4, 0)
+    lat, fails = [], 0
+    try:
+        tickets = []
+        t0 = time.perf_counter()
+        for q in qs:
+            while time.perf_counter() - t0 < q["t"]:
+                time.sleep(0.0005)
+            tickets.append(hbx.hbx_submit(tc.ctx, srv, handles[q["graph"]], q["model"], q["k"], q["eps"], 1.0,
+                                          7 + q["graph"]))
+        for q, t in zip(qs, tickets):
+            rc, res = hbx.hbx_wait(t, q["k"])
+            hbx.hbx_ticket_destroy(t)
+            if rc != 0:
+                fails += 1
+                continue
+            lat.append(res["latency_s"])
+        wall = time.perf_counter() - t0
+    finally:
+        hbx.hbx_server_destroy(srv)
+        for h in handles:
+            hbx.hbx_graph_destroy(h)
+    lat = np.array(lat) if lat else np.zeros(1)
+    return {"queries": count, "failed": fails, "rate_per_s": rate, "queries_per_s": (count - fails) / wall,
+            "wall_s": wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_inflight": 4,
+            "graphs": "ic_rmat4k, wc_rmat1m, lt_rmat4m shapes (IC probabilities and LT weights on each)"}
 
 
 def run_reference(args, rank):
@@ -262,6 +321,9 @@ def run_hbx(args, rank, world, local_rank):
                  "encode": "int32", "batched_speedup": pmean / (total_ms / args.steps),
                  "seeds_equal": bool(np.array_equal(pr["seeds"], r["seeds"])),
                  "influence_equal": pr["influence"] == r["influence"]}
+    serving = None
+    if args.serving:
+        serving = serving_leg(hbx, synth, tc, {w.name: g}, args.serving)
     # roofline of the dominant kernel (sampling fused with encoding)
     peak, peak_kind = peaks()
     alg_bytes = sum(8 * s["rr_vertices"] + 4 * s["edges_scanned"] + 4 * s["edges_live"] + s["pool_bytes"]
@@ -308,8 +370,10 @@ def run_hbx(args, rank, world, local_rank):
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "sampler: warp, shared-memory block and HBM block kernels, encode fused",
                      "launches": klaunch, "kernel_s": ksec},
+        "count_roofline": count_roofline(stats, peak),
         "cpu_baseline": cpu,
         "plain_form": plain,
+        "serving": serving,
         "clocks": clk,
     }
     print(json.dumps(out), flush=True)
@@ -344,6 +408,7 @@ def main():
     ap.add_argument("--encode", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison leg")
+    ap.add_argument("--serving", type=int, default=0, help="queries of the serving leg (0: skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

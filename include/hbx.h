@@ -121,6 +121,12 @@ typedef struct {
     /* every kernel the library launched for this pool or query (graph nodes
      * included) */
     uint64_t kernel_launches;
+    /* device time (CUDA events) of the selections' count passes -- the initial
+     * per-vertex occurrence counts over the sets each selection counted -- and
+     * the bytes those passes read: 4 per heap word of the counted sets, 16 per
+     * set record, 8 per chunk item and 4 per bitmap-list entry */
+    double count_kernel_s;
+    uint64_t count_bytes;
 } hbx_stats;
 
 /* Human-readable name of an HBX_ERR_* code. */

@@ -48,7 +48,8 @@ class hbx_stats(ctypes.Structure):
                 ("warp_group_budget", ctypes.c_uint32), ("block_cluster", ctypes.c_uint32)] + \
                [(f, ctypes.c_double) for f in ["lb", "sample_s", "select_s", "total_s", "skewness", "density",
                                                 "sample_kernel_s"]] + \
-               [("sample_kernel_launches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+               [("sample_kernel_launches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("count_kernel_s", ctypes.c_double), ("count_bytes", ctypes.c_uint64)]
 
     def to_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -26,6 +26,7 @@ struct SelState {
 
 struct SelArgs {
     uint32_t n, n4, T;
+    uint32_t j_lo;                         // count passes over uncompressed sets: [j_lo, T)
     const SetRec* recs;
     const uint32_t* raw_heap;
     const uint32_t* code_heap;

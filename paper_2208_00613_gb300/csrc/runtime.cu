@@ -882,6 +882,7 @@ int pool_extend(hbx_pool* p, uint64_t T) {
         p->launches++;
         RC(read_counters(p));
         p->T = j0 + count;
+        p->bounds[p->T] = {p->hc.chunk_items, p->hc.bm_list, p->hc.words_used};
     }
     p->sample_s += now_s() - t0;
     return HBX_OK;
@@ -965,7 +966,42 @@ static int pool_select_launch(hbx_pool* p, uint64_t T, uint32_t k, cudaStream_t 
     const SelArgs a = sel_args(p, T);
     const uint32_t enc = p->o.encode;
     CK(launch_sel_init(a, st));
-    CK(launch_count(a, enc, st));
+    // The batched form counts incrementally: the undecremented counts of the
+    // last selection's prefix [0, base_T) are restored and only the sets
+    // [base_T, T) are counted (their chunk items and bitmap entries follow the
+    // prefix's, base_T being a batch end).
+    SelArgs c = a;
+    const size_t cbytes = (size_t)a.n4 * 4;
+    const auto bd = p->bounds.find(p->base_T);
+    uint64_t words_lo = 0;
+    if (p->o.form && p->base_T && p->base_T <= T && bd != p->bounds.end()) {
+        CK(cudaMemcpyAsync(p->cnt, p->cnt_base, cbytes, cudaMemcpyDeviceToDevice, st));
+        c.chunk_items = p->items + bd->second.items;
+        c.n_items = a.n_items - bd->second.items;
+        c.bm_sets = p->bm_sets + bd->second.bm;
+        c.n_bm = a.n_bm - (uint32_t)bd->second.bm;
+        c.j_lo = (uint32_t)p->base_T;
+        words_lo = bd->second.words;
+    }
+    if (!p->evc0) {
+        CK(cudaEventCreate(&p->evc0));
+        CK(cudaEventCreate(&p->evc1));
+    }
+    CK(cudaEventRecord(p->evc0, st));
+    CK(launch_count(c, enc, st));
+    CK(cudaEventRecord(p->evc1, st));
+    p->count_pending = true;
+    {
+        const auto hi = p->bounds.find(T);
+        const uint64_t words_hi = hi != p->bounds.end() ? hi->second.words : p->hc.words_used;
+        p->count_bytes += 4 * (words_hi - std::min(words_hi, words_lo)) + 16 * (T - c.j_lo) + 8 * c.n_items +
+                          4ull * c.n_bm;
+    }
+    if (p->o.form && p->bounds.count(T)) {
+        if (!p->cnt_base) RC(grow_buffer(p, (void**)&p->cnt_base, 0, cbytes, 0));
+        CK(cudaMemcpyAsync(p->cnt_base, p->cnt, cbytes, cudaMemcpyDeviceToDevice, st));
+        p->base_T = T;
+    }
     const uint64_t per_it = 3 + (enc ? (uint64_t)(a.has_cb ? 1 : 0) + (a.n_bm ? 1 : 0) : 1);
     p->launches += 1 + (enc ? (uint64_t)((a.n_items && a.has_cb) ? 1 : 0) + (a.n_bm ? 1 : 0) : 1) + per_it * k;
     if (p->o.form) {
@@ -1007,6 +1043,12 @@ static int pool_select_finish(hbx_pool* p, uint32_t k, uint32_t* seeds, uint64_t
     CK(cudaMemcpyAsync(seeds, p->d_seeds, (size_t)k * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hm.data(), p->d_marg, (size_t)k * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (p->count_pending) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, p->evc0, p->evc1));
+        p->count_kernel_s += ms * 1e-3;
+        p->count_pending = false;
+    }
     if (hs.pad == 1) return fail(ctx, HBX_ERR_INTERNAL, "undecodable Huffman stream during selection");
     if (hs.pad) return fail(ctx, HBX_ERR_INTERNAL, "decrement item list overflow during selection");
     if (hs.it != k) return fail(ctx, HBX_ERR_INTERNAL, "selection ran " + std::to_string(hs.it) + " iterations");
@@ -1079,10 +1121,12 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
                     p->code_of_rank, p->len_of_rank, p->lut, p->dec, p->items, p->bm_sets, p->big_list,
                     p->retry_list, p->list_in, p->giant_list, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
                     p->alive, p->cov_huff, p->cov_bm, p->cov_raw, p->st, p->partials, p->ticket, p->d_seeds,
-                    p->d_marg, p->dec_items};
+                    p->d_marg, p->dec_items, p->cnt_base};
     for (void* b : bufs) dfree(c, b);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->evc0) cudaEventDestroy(p->evc0);
+    if (p->evc1) cudaEventDestroy(p->evc1);
     if (p->own_stream) cudaStreamDestroy(p->stream);
     {
         std::lock_guard<std::mutex> lock(c->mu);
@@ -1186,6 +1230,8 @@ void fill_stats(hbx_pool* p, hbx_stats* s) {
     s->sample_kernel_s = p->sample_kernel_s;
     s->sample_kernel_launches = p->sample_kernel_launches;
     s->kernel_launches = p->launches;
+    s->count_kernel_s = p->count_kernel_s;
+    s->count_bytes = p->count_bytes;
 }
 
 int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds, double* influence,

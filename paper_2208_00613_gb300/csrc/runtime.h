@@ -98,6 +98,19 @@ struct hbx_pool {
     uint64_t bp_words = 0;
     // selection state
     int32_t* cnt = nullptr;
+    // counts of sets [0, base_T) before any decrement, kept for the next
+    // selection on a longer prefix; bounds: pool size at each batch end ->
+    // (chunk items, bitmap list entries) of the sets below it
+    int32_t* cnt_base = nullptr;
+    uint64_t base_T = 0;
+    struct Bound {
+        uint64_t items, bm, words;  // chunk items, bitmap-list entries, heap words of the sets below
+    };
+    std::map<uint64_t, Bound> bounds;
+    double count_kernel_s = 0;
+    uint64_t count_bytes = 0;
+    cudaEvent_t evc0 = nullptr, evc1 = nullptr;
+    bool count_pending = false;
     uint8_t* alive = nullptr;
     uint64_t alive_cap = 0;
     uint32_t *cov_huff = nullptr, *cov_bm = nullptr, *cov_raw = nullptr;

@@ -708,7 +708,7 @@ __device__ void block_walk_lt(const SampleArgs& a, uint32_t j, uint32_t* visited
 // One heavy set per thread-block cluster (a cluster of 1 is a plain block).
 // Block 0 of the cluster owns the set's bookkeeping in its shared memory, and
 // encodes the set once the cluster has finished the search.
-__global__ void __launch_bounds__(BP_THREADS) sample_block_kernel(SampleArgs a, uint32_t nbig) {
+__global__ void __launch_bounds__(BP_THREADS, 2) sample_block_kernel(SampleArgs a, uint32_t nbig) {
     __shared__ BlockShared s;
     cg::cluster_group cl = cg::this_cluster();
     const uint32_t crank = cl.block_rank(), csize = cl.num_blocks();
@@ -979,7 +979,7 @@ struct MidShared {
     uint32_t ee[BP_THREADS];
     uint32_t warp[33];
     uint32_t stage[40];
-    uint32_t tail, item;
+    uint32_t tail, item, head;
     int overflow, fail;
 };
 
@@ -1003,6 +1003,110 @@ __device__ __forceinline__ void mid_append(const SampleArgs& a, MidShared& s, ui
             s.overflow = 1;
         }
     }
+}
+
+constexpr uint32_t MID_WARP_GROUPS = 512;  // a chunk with more edge groups goes to the whole block
+
+// Warp 0 of the block expands the queue alone, 32 vertices at a time in FIFO
+// order, while the unexpanded vertices fit one warp and their edge groups stay
+// under MID_WARP_GROUPS; the rest of the block waits at a barrier.  Deep sets
+// with thin frontiers then advance without block barriers.  Each lane takes
+// BP_ILP edge groups per pass, and the live edges' col loads are issued four
+// at a time before their inserts.  Returns the new head; s.tail is updated.
+__device__ uint32_t mid_warp_run(const SampleArgs& a, MidShared& s, uint32_t* Q, uint32_t* QB, uint32_t* QE,
+                                 uint32_t* H, uint32_t j, uint32_t head, unsigned long long* scanned,
+                                 unsigned long long* live) {
+    constexpr uint32_t HMASK = BQ_HASH - 1;
+    constexpr uint32_t HSHIFT = 32 - __builtin_ctz(BQ_HASH);
+    const uint32_t lane = lane_id();
+    uint32_t tail = s.tail;
+    bool overflow = false;
+    while (head < tail && tail - head <= 32 && !overflow) {
+        const uint32_t cnt = tail - head;
+        uint32_t b = 0, e = 0, ng = 0, gfirst = 0;
+        if (lane < cnt) {
+            b = QB[head + lane];
+            e = QE[head + lane];
+            if (e > b) {
+                gfirst = b >> 2;
+                ng = ((e - 1) >> 2) - gfirst + 1;
+            }
+        }
+        const uint32_t incl = warp_incl_scan(ng);
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (total > MID_WARP_GROUPS) break;
+        s.scan[lane] = incl;
+        s.g0[lane] = gfirst;
+        s.eb[lane] = b;
+        s.ee[lane] = e;
+        __syncwarp();
+        for (uint32_t base = 0; base < total && !overflow; base += 32 * BP_ILP) {
+            uint32_t gg[BP_ILP], eb[BP_ILP], ee[BP_ILP];
+#pragma unroll
+            for (int q = 0; q < BP_ILP; q++) {
+                const uint32_t t = base + q * 32 + lane;
+                gg[q] = 0;
+                eb[q] = 0;
+                ee[q] = 0;
+                if (t < total) {
+                    uint32_t lo = 0, hi = cnt - 1;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (s.scan[mid] > t) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    gg[q] = s.g0[lo] + (t - (lo ? s.scan[lo - 1] : 0u));
+                    eb[q] = s.eb[lo];
+                    ee[q] = s.ee[lo];
+                }
+            }
+            uint32_t m = 0;
+#pragma unroll
+            for (int q = 0; q < BP_ILP; q++)
+                if (ee[q] > eb[q]) m |= group_coins(a, j, gg[q], eb[q], ee[q], scanned) << (4 * q);
+            *live += __popc(m);
+            while (__any_sync(0xFFFFFFFFu, m != 0) && !overflow) {
+                uint32_t u[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    u[k] = NONE;
+                    if (m) {
+                        const uint32_t bit = __ffs(m) - 1;
+                        m &= m - 1;
+                        uint32_t g = gg[0];
+#pragma unroll
+                        for (int q = 1; q < BP_ILP; q++)
+                            if ((bit >> 2) == (uint32_t)q) g = gg[q];
+                        u[k] = __ldg(a.g.col + g * 4u + (bit & 3u));
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const bool isnew = u[k] != NONE && hash_insert(H, HMASK, HSHIFT, u[k], a.ctr);
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isnew);
+                    if (!bal) continue;
+                    const uint32_t pos = tail + __popc(bal & lanemask_lt());
+                    if (isnew && pos < BQ) {
+                        Q[pos] = u[k];
+                        QB[pos] = __ldg(a.g.row_ptr + u[k]);
+                        QE[pos] = __ldg(a.g.row_ptr + u[k] + 1);
+                    }
+                    tail += __popc(bal);
+                    if (tail > BQ) {
+                        overflow = true;
+                        break;
+                    }
+                }
+            }
+        }
+        head += cnt;
+        __syncwarp();
+    }
+    if (lane == 0) {
+        s.tail = tail;
+        if (overflow) s.overflow = 1;
+    }
+    return head;
 }
 
 __global__ void __launch_bounds__(BP_THREADS) sample_mid_kernel(SampleArgs a, uint32_t nbig) {
@@ -1042,10 +1146,26 @@ __global__ void __launch_bounds__(BP_THREADS) sample_mid_kernel(SampleArgs a, ui
         if (a.model == MODEL_IC) {
             uint32_t head = 0;
             for (;;) {
-                const uint32_t tail = s.tail;  // the previous level ended with a barrier
+                const uint32_t tail = s.tail;  // the previous step ended with a barrier
                 if (head >= tail || s.overflow) break;
-                for (uint32_t c0 = head; c0 < tail; c0 += BP_THREADS) {
-                    const uint32_t cnt = min((uint32_t)BP_THREADS, tail - c0);
+                if (tail - head <= 32) {
+                    // thin frontier: warp 0 runs ahead alone
+                    const uint32_t h0 = head;
+                    if (warp == 0) {
+                        const uint32_t nh = mid_warp_run(a, s, Q, QB, QE, H, j, head, &set_scanned, &set_live);
+                        if (lane == 0) s.head = nh;
+                    }
+                    __syncthreads();
+                    head = s.head;
+                    if (head != h0) {
+                        __syncthreads();  // everyone has read s.head before it changes
+                        continue;
+                    }
+                    // no progress: the chunk's edge groups are too many for one warp
+                }
+                const uint32_t ltail = s.tail;
+                for (uint32_t c0 = head; c0 < ltail; c0 += BP_THREADS) {
+                    const uint32_t cnt = min((uint32_t)BP_THREADS, ltail - c0);
                     uint32_t b = 0, e = 0, ng = 0, gfirst = 0;
                     if (tid < cnt) {
                         b = QB[c0 + tid];
@@ -1110,7 +1230,7 @@ __global__ void __launch_bounds__(BP_THREADS) sample_mid_kernel(SampleArgs a, ui
                     }
                     __syncthreads();
                 }
-                head = tail;
+                head = ltail;
             }
         } else if (warp == 0) {
             uint32_t v = Q[0], tail = 1;

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(SEL_THREADS) bitmap_count_kernel(SelArgs a, co
 __global__ void count_raw_kernel(SelArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < a.T; j += nwarps) {
+    for (uint32_t j = a.j_lo + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < a.T; j += nwarps) {
         const SetRec rec = a.recs[j];
         const uint32_t* x = a.raw_heap + rec_off(rec);
         for (uint32_t i = lane; i < rec.size; i += 32) atomicAdd(&a.cnt[x[i]], 1);

@@ -72,12 +72,12 @@ def test_pool_memory_limit(small_graph):
     w, g = small_graph
     with hbx.torch_context(0) as tc:
         G = hbx.hbx_graph_create(tc.ctx, g)
-        p = hbx.hbx_pool_create(tc.ctx, G, "IC", w.rr_seed, hbx.hbx_default_options(max_device_bytes=1 << 16))
+        p = hbx.hbx_pool_create(tc.ctx, G, "IC", w.rr_seed, hbx.hbx_default_options(encode=0, max_device_bytes=1 << 16))
         with pytest.raises(hbx.HbxError) as e:
             hbx.hbx_pool_extend(tc.ctx, p, 1000)
         assert e.value.code == HBX_ERR_OOM
         hbx.hbx_pool_destroy(p)
-        p = hbx.hbx_pool_create(tc.ctx, G, "IC", w.rr_seed, hbx.hbx_default_options())
+        p = hbx.hbx_pool_create(tc.ctx, G, "IC", w.rr_seed, hbx.hbx_default_options(encode=0))
         hbx.hbx_pool_extend(tc.ctx, p, 1000)
         assert hbx.hbx_pool_size(p) == 1000
         hbx.hbx_pool_destroy(p)

@@ -240,6 +240,29 @@ def test_select_tiny(ctx, enc, form):
     hbx.hbx_graph_destroy(G)
 
 
+@pytest.mark.parametrize("enc", [0, 1])
+def test_select_incremental_counts(ctx, enc):
+    # selections on growing prefixes of one pool restore the previous prefix's
+    # counts and count only the new sets; each must equal the oracle's greedy
+    w = synth.WORKLOADS["ic_rmat4k"]
+    g = workload_graph("ic_rmat4k")
+    G = hbx.hbx_graph_create(ctx, g)
+    p = hbx.hbx_pool_create(ctx, G, "IC", w.rr_seed, opts(encode=enc, form=1, warmup_sets=300, density_cut=8))
+    op = oracle.Pool(g, oracle.IC, w.rr_seed)
+    op.extend(6000)
+    for T, TT, k in [(1000, 1000, 12), (2500, 2500, 12), (2500, 1700, 5), (6000, 6000, 25), (6000, 3001, 7)]:
+        hbx.hbx_pool_extend(ctx, p, T)
+        s, m, c = hbx.hbx_pool_select(ctx, p, TT, k)
+        so, mo, co = op.greedy(TT, k)
+        assert s.tolist() == so.tolist(), (T, TT)
+        assert m.tolist() == mo.tolist(), (T, TT)
+        assert c == co
+    if enc:
+        assert hbx.hbx_pool_stats(ctx, p)["sets_bitmap"] > 0
+    hbx.hbx_pool_destroy(p)
+    hbx.hbx_graph_destroy(G)
+
+
 @pytest.mark.parametrize("enc,form", [(0, 0), (1, 1)])
 def test_imm_tiny(ctx, enc, form):
     w = synth.WORKLOADS["ic_rmat4k"]
