@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhbx.so")
-SOURCES = ["sample.cu", "select.cu", "runtime.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["sample.cu", "msbfs.cu", "select.cu", "runtime.cu", "server.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -143,6 +143,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
+__device__ __forceinline__ void set_error(Counters* c, unsigned long long code) { atomicMax(&c->error, code); }
+
+// IC coin of Section 2.1: edge e is live in sample j when the top 24 bits of
+// its Philox word, as a fraction of 2^24 (exact in fp32), fall below p(e).
+__device__ __forceinline__ bool ic_live(uint32_t x, float p) { return (float)(x >> 8) * 0x1p-24f < p; }
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

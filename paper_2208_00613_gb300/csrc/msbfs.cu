@@ -1,0 +1,354 @@
+// Bit-parallel reverse BFS for the IC sets that outgrow shared memory.
+//
+// Under IC (Section 2.1) the RR set of sample j is the set of vertices that
+// reach its root through edges whose coin, drawn from Philox at (edge group,
+// j, epoch, 1), is live.  The set does not depend on the order in which the
+// search visits vertices, so up to 32 such sets are searched together, one
+// bit per set: vis[v], cur[v] and nxt[v] are 32-bit masks (visited, this
+// level's frontier, next level's frontier), and a vertex is expanded once per
+// level for every set whose frontier holds it.  Its in-edge probabilities and
+// sources are then read once for all of those sets, and each set still draws
+// its own coin for every in-edge of every vertex it visits, so the sets, their
+// scanned and live edge counts are those of one search per set.
+//
+// A level is two launches: the light kernel takes the frontier list 32
+// vertices per warp (edge groups spread over the lanes by a warp prefix sum)
+// and moves vertices with more than MS_HEAVY groups to a list of chunks of
+// MS_CHUNK groups, which the heavy kernel then spreads over whole blocks.
+// The host advances levels until the frontier is empty, then a tally pass
+// gives each set's size and scanned edges, and the emit pass writes the
+// dense sets' bitmap rows (a 32 x 32 bit transpose per warp through shared
+// memory) and clears the masks for the next batch.
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace hbx {
+
+constexpr int MS_THREADS = 256;
+constexpr int MS_WARPS = MS_THREADS / 32;
+constexpr uint32_t MS_HEAVY = 1024;  // edge groups above which a vertex is split into chunks
+constexpr uint32_t MS_CHUNK = 4096;  // edge groups per chunk of a heavy vertex
+
+// Live-edge counts per set are kept per lane (s_live[warp][set][lane]: every
+// lane owns a column, so the updates need no atomics and hit distinct banks)
+// and summed when the block ends.
+using LiveCounts = uint32_t[MS_WARPS][MS_SETS][32];
+
+__device__ __forceinline__ void ms_init_shared(const MsArgs& a, uint32_t* s_sets, LiveCounts& s_live) {
+    if (threadIdx.x < MS_SETS) s_sets[threadIdx.x] = threadIdx.x < a.nsets ? a.sets[threadIdx.x] : 0u;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (uint32_t s = 0; s < MS_SETS; s++) s_live[warp][s][lane] = 0;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void ms_flush_live(const MsArgs& a, const LiveCounts& s_live) {
+    __syncthreads();
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // warp w sums sets w, w + MS_WARPS, ... over every warp's lanes
+    for (uint32_t s = warp; s < MS_SETS; s += MS_WARPS) {
+        unsigned long long t = 0;
+        for (uint32_t w = 0; w < MS_WARPS; w++) t += s_live[w][s][lane];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        if (lane == 0 && t) atomicAdd(&a.mc->live[s], t);
+    }
+}
+
+// Append the vertices flagged by the lanes of a warp to the next frontier
+// list (one atomic per warp).  Called by every lane of the warp.
+__device__ __forceinline__ void ms_append(const MsArgs& a, bool app, uint32_t u) {
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, app);
+    if (!bal) return;
+    const uint32_t lane = lane_id(), leader = __ffs(bal) - 1;
+    uint32_t pos = 0;
+    if (lane == leader) pos = atomicAdd(&a.mc->nN, (uint32_t)__popc(bal));
+    pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+    if (app) a.N[pos + __popc(bal & lanemask_lt())] = u;
+}
+
+// One aligned group of 4 in-edges gg of a frontier vertex whose in-edges are
+// [eb, ee), for the sets in mask f.  Every lane of the warp calls it (valid
+// false for lanes without a group).
+__device__ __forceinline__ void ms_group(const MsArgs& a, const uint32_t* s_sets, LiveCounts& s_live,
+                                         bool valid, uint32_t gg, uint32_t eb, uint32_t ee, uint32_t f) {
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t em0 = 0, em1 = 0, em2 = 0, em3 = 0;  // sets for which edge 4gg+k is live
+    if (valid) {
+        const float4 p4 = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
+        const uint32_t e0 = gg * 4u;
+        const bool v0 = e0 >= eb && e0 < ee, v1 = e0 + 1 >= eb && e0 + 1 < ee;
+        const bool v2 = e0 + 2 >= eb && e0 + 2 < ee, v3 = e0 + 3 >= eb && e0 + 3 < ee;
+        while (f) {
+            const uint32_t s = __ffs(f) - 1;
+            f &= f - 1;
+            const uint4 x = philox4x32_10(make_uint4(gg, s_sets[s], a.epoch, STREAM_IC), a.key0, a.key1);
+            const uint32_t l0 = v0 && ic_live(x.x, p4.x), l1 = v1 && ic_live(x.y, p4.y);
+            const uint32_t l2 = v2 && ic_live(x.z, p4.z), l3 = v3 && ic_live(x.w, p4.w);
+            const uint32_t nl = l0 + l1 + l2 + l3;
+            if (nl) {
+                s_live[warp][s][lane] += nl;
+                em0 |= l0 << s;
+                em1 |= l1 << s;
+                em2 |= l2 << s;
+                em3 |= l3 << s;
+            }
+        }
+    }
+    const uint32_t em[4] = {em0, em1, em2, em3};
+    uint32_t u[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) u[k] = em[k] ? __ldg(a.g.col + gg * 4u + k) : NONE;
+    bool app[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        app[k] = false;
+        if (em[k]) {
+            const uint32_t fresh = em[k] & ~atomicOr(&a.vis[u[k]], em[k]);
+            if (fresh) app[k] = atomicOr(&a.nxt[u[k]], fresh) == 0u;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) ms_append(a, app[k], u[k]);
+}
+
+// Roots of the batch's sets: visited and in the first frontier.  <<<1, 32>>>
+__global__ void ms_start_kernel(MsArgs a) {
+    const uint32_t s = threadIdx.x;
+    bool app = false;
+    uint32_t root = 0;
+    if (s < a.nsets) {
+        const uint4 rr = philox4x32_10(make_uint4(0u, a.sets[s], a.epoch, STREAM_ROOT), a.key0, a.key1);
+        root = __umulhi(rr.x, a.g.n);
+        atomicOr(&a.vis[root], 1u << s);
+        app = atomicOr(&a.cur[root], 1u << s) == 0u;
+    }
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, app);
+    if (app) a.F[__popc(bal & lanemask_lt())] = root;
+    if (s == 0) a.mc->nF = __popc(bal);
+}
+
+__global__ void __launch_bounds__(MS_THREADS) ms_light_kernel(MsArgs a) {
+    __shared__ uint32_t s_sets[MS_SETS];
+    __shared__ LiveCounts s_live;
+    __shared__ uint32_t w_scan[MS_WARPS][32], w_g0[MS_WARPS][32], w_eb[MS_WARPS][32], w_ee[MS_WARPS][32],
+        w_f[MS_WARPS][32];
+    ms_init_shared(a, s_sets, s_live);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t nF = a.mc->nF;
+    const uint32_t stride = gridDim.x * MS_WARPS * 32;
+    for (uint32_t c = (blockIdx.x * MS_WARPS + warp) * 32; c < nF; c += stride) {
+        const uint32_t i = c + lane;
+        uint32_t v = 0, f = 0, b = 0, e = 0, gfirst = 0, ng = 0;
+        if (i < nF) {
+            v = a.F[i];
+            f = a.cur[v];
+            a.cur[v] = 0u;  // cur becomes the next level's nxt and must be clear
+            b = __ldg(a.g.row_ptr + v);
+            e = __ldg(a.g.row_ptr + v + 1);
+            if (e > b) {
+                gfirst = b >> 2;
+                ng = ((e - 1) >> 2) - gfirst + 1;
+            }
+            if (ng > MS_HEAVY) {
+                // heavy vertex: its groups go to whole blocks in chunks
+                for (uint32_t g = gfirst; g < gfirst + ng; g += MS_CHUNK) {
+                    const uint32_t h = atomicAdd(&a.mc->nH, 1u);
+                    if (h < a.heavy_cap) a.heavy[h] = make_uint4(v, g, min(g + MS_CHUNK, gfirst + ng), f);
+                    else set_error(a.ctr, 5);
+                }
+                ng = 0;
+            }
+        }
+        const uint32_t incl = warp_incl_scan(ng);
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        w_scan[warp][lane] = incl;
+        w_g0[warp][lane] = gfirst;
+        w_eb[warp][lane] = b;
+        w_ee[warp][lane] = e;
+        w_f[warp][lane] = f;
+        __syncwarp();
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t t = base + lane;
+            const bool valid = t < total;
+            uint32_t gg = 0, eb = 0, ee = 0, ff = 0;
+            if (valid) {
+                uint32_t lo = 0, hi = 31;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (w_scan[warp][mid] > t) hi = mid;
+                    else lo = mid + 1;
+                }
+                gg = w_g0[warp][lo] + (t - (lo ? w_scan[warp][lo - 1] : 0u));
+                eb = w_eb[warp][lo];
+                ee = w_ee[warp][lo];
+                ff = w_f[warp][lo];
+            }
+            ms_group(a, s_sets, s_live, valid, gg, eb, ee, ff);
+        }
+        __syncwarp();
+    }
+    ms_flush_live(a, s_live);
+}
+
+__global__ void __launch_bounds__(MS_THREADS) ms_heavy_kernel(MsArgs a) {
+    __shared__ uint32_t s_sets[MS_SETS];
+    __shared__ LiveCounts s_live;
+    ms_init_shared(a, s_sets, s_live);
+    const uint32_t nH = min(a.mc->nH, a.heavy_cap);
+    for (uint32_t it = blockIdx.x; it < nH; it += gridDim.x) {
+        const uint4 item = a.heavy[it];
+        const uint32_t eb = __ldg(a.g.row_ptr + item.x), ee = __ldg(a.g.row_ptr + item.x + 1);
+        for (uint32_t g = item.y; g < item.z; g += MS_THREADS) {
+            const uint32_t gg = g + threadIdx.x;
+            ms_group(a, s_sets, s_live, gg < item.z, gg, eb, ee, item.w);
+        }
+    }
+    ms_flush_live(a, s_live);
+}
+
+// Next level: the list just filled becomes the frontier.  <<<1, 1>>>
+__global__ void ms_advance_kernel(MsArgs a) {
+    a.mc->nF = a.mc->nN;
+    a.mc->nN = 0;
+    a.mc->nH = 0;
+}
+
+// Size and scanned in-edges of each set of the batch, from the visited masks:
+// lane s of every warp keeps set s's totals.
+__global__ void __launch_bounds__(MS_THREADS) ms_tally_kernel(MsArgs a) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n = a.g.n;
+    unsigned long long size = 0, scanned = 0;
+    const uint32_t stride = gridDim.x * MS_THREADS;
+    for (uint32_t v0 = blockIdx.x * MS_THREADS + (threadIdx.x & ~31u); v0 < n; v0 += stride) {
+        const uint32_t v = v0 + lane;
+        uint32_t m = 0, d = 0;
+        if (v < n) {
+            m = a.vis[v];
+            if (m) d = __ldg(a.g.row_ptr + v + 1) - __ldg(a.g.row_ptr + v);
+        }
+        uint32_t any = __reduce_or_sync(0xFFFFFFFFu, m);
+        while (any) {
+            const uint32_t s = __ffs(any) - 1;
+            any &= any - 1;
+            const bool in = (m >> s) & 1u;
+            const uint32_t cnt = __popc(__ballot_sync(0xFFFFFFFFu, in));
+            const uint32_t sd = __reduce_add_sync(0xFFFFFFFFu, in ? d : 0u);
+            if (lane == s) {
+                size += cnt;
+                scanned += sd;
+            }
+        }
+    }
+    if (size) atomicAdd(&a.mc->size[lane], size);
+    if (scanned) atomicAdd(&a.mc->scanned[lane], scanned);
+}
+
+// Bitmap rows of the dense sets (bit s of mask `dense`; row of set s at word
+// offset rowoff[s] of the bitmap heap), and the masks cleared for the next
+// batch.  A warp takes 32 words (1024 vertices) at a time.
+__global__ void __launch_bounds__(MS_THREADS) ms_emit_kernel(MsArgs a, uint32_t dense, uint32_t* bm_heap) {
+    __shared__ uint32_t tile[MS_WARPS][32][33];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t n = a.g.n, nw = (n + 31) / 32;
+    const uint32_t nchunks = (nw + 31) / 32;
+    for (uint32_t c = blockIdx.x * MS_WARPS + warp; c < nchunks; c += gridDim.x * MS_WARPS) {
+        for (uint32_t wi = 0; wi < 32; wi++) {
+            const uint32_t v = (c * 32 + wi) * 32 + lane;
+            uint32_t m = 0;
+            if (v < n) {
+                m = a.vis[v];
+                if (m) a.vis[v] = 0u;
+            }
+            uint32_t ds = dense;
+            while (ds) {
+                const uint32_t s = __ffs(ds) - 1;
+                ds &= ds - 1;
+                const uint32_t r = __ballot_sync(0xFFFFFFFFu, (m >> s) & 1u);
+                if (lane == 0) tile[warp][s][wi] = r;
+            }
+        }
+        __syncwarp();
+        const uint32_t w = c * 32 + lane;
+        uint32_t ds = dense;
+        while (ds) {
+            const uint32_t s = __ffs(ds) - 1;
+            ds &= ds - 1;
+            if (w < nw) bm_heap[a.rowoff[s] + w] = tile[warp][s][lane];
+        }
+        __syncwarp();
+    }
+}
+
+// Records and pool counters of the batch's dense sets (MODE_ENCODE), or the
+// dense-set count of a histogram pass.  <<<1, 32>>>
+__global__ void ms_commit_kernel(MsArgs a, uint32_t dense, uint32_t mode, uint64_t row_words) {
+    const uint32_t s = threadIdx.x;
+    const bool d = (dense >> s) & 1u;
+    unsigned long long verts = 0, sc = 0, lv = 0;
+    if (d && mode == MODE_ENCODE) {
+        a.recs[a.sets[s]] = make_rec(KIND_BITMAP, a.rowoff[s], (uint32_t)a.mc->size[s], 0);
+        verts = a.mc->size[s];
+        sc = a.mc->scanned[s];
+        lv = a.mc->live[s];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        verts += __shfl_xor_sync(0xFFFFFFFFu, verts, o);
+        sc += __shfl_xor_sync(0xFFFFFFFFu, sc, o);
+        lv += __shfl_xor_sync(0xFFFFFFFFu, lv, o);
+    }
+    if (s == 0) {
+        const unsigned long long nd = (unsigned long long)__popc(dense);
+        if (mode == MODE_HIST) {
+            atomicAdd(&a.ctr->hist_dense, nd);
+        } else if (nd) {
+            atomicAdd(&a.ctr->sets_bm, nd);
+            atomicAdd(&a.ctr->sets_big, nd);
+            atomicAdd(&a.ctr->rr_vertices, verts);
+            atomicAdd(&a.ctr->words_used, nd * row_words);
+            atomicAdd(&a.ctr->edges_scanned, sc);
+            atomicAdd(&a.ctr->edges_live, lv);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static uint32_t ms_grid(const void* kernel, int sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, MS_THREADS, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return (uint32_t)(sms * (per_sm > 0 ? per_sm : 1));
+}
+
+cudaError_t launch_ms_start(const MsArgs& a, cudaStream_t s) {
+    ms_start_kernel<<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ms_level(const MsArgs& a, int sms, cudaStream_t s) {
+    static const uint32_t gl = ms_grid((const void*)ms_light_kernel, sms);
+    static const uint32_t gh = ms_grid((const void*)ms_heavy_kernel, sms);
+    ms_light_kernel<<<gl, MS_THREADS, 0, s>>>(a);
+    ms_heavy_kernel<<<gh, MS_THREADS, 0, s>>>(a);
+    ms_advance_kernel<<<1, 1, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ms_finish(const MsArgs& a, int sms, cudaStream_t s) {
+    ms_tally_kernel<<<(uint32_t)sms * 4, MS_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ms_emit(const MsArgs& a, uint32_t dense, uint32_t mode, uint64_t row_words, uint32_t* bm_heap,
+                           int sms, cudaStream_t s) {
+    ms_emit_kernel<<<(uint32_t)sms * 2, MS_THREADS, 0, s>>>(a, mode == MODE_ENCODE ? dense : 0u, bm_heap);
+    ms_commit_kernel<<<1, 32, 0, s>>>(a, dense, mode, row_words);
+    return cudaGetLastError();
+}
+
+}  // namespace hbx

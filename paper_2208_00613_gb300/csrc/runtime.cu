@@ -351,7 +351,9 @@ static const uint64_t HEAP_SLACK = 64;  // words past the end, for the decoder's
 
 static int grow_heap(hbx_pool* p, Heap& h, uint64_t need_words, bool exact = false) {
     if (need_words <= h.cap) return HBX_OK;
-    uint64_t nc = exact ? need_words : std::max<uint64_t>(need_words + need_words / 4, h.cap * 2);
+    // doubling, or growth by a quarter once the heap passes 8 GB
+    const uint64_t step = h.cap * 4 > (8ull << 30) ? h.cap / 4 : h.cap;
+    uint64_t nc = exact ? need_words : std::max<uint64_t>(need_words + need_words / 8, h.cap + step);
     nc = std::max<uint64_t>(nc, 1u << 16);
     nc = (nc + 3) & ~3ull;
     RC(grow_buffer(p, (void**)&h.d, h.d ? (h.cap + HEAP_SLACK) * 4 : 0, (nc + HEAP_SLACK) * 4, h.cap * 4));
@@ -496,6 +498,110 @@ static int run_block_path(hbx_pool* p, SampleArgs a, uint32_t nitems, uint32_t c
     return timed_launch(p, timed, [&] { return launch_sample_block(a, nitems, slots, csize, p->stream); });
 }
 
+static int ensure_ms_scratch(hbx_pool* p) {
+    if (p->ms_vis) return HBX_OK;
+    const uint64_t n4 = (uint64_t)p->g->n * 4;
+    RC(grow_buffer(p, (void**)&p->ms_vis, 0, n4, 0));
+    RC(grow_buffer(p, (void**)&p->ms_cur, 0, n4, 0));
+    RC(grow_buffer(p, (void**)&p->ms_nxt, 0, n4, 0));
+    RC(grow_buffer(p, (void**)&p->ms_F, 0, n4, 0));
+    RC(grow_buffer(p, (void**)&p->ms_N, 0, n4, 0));
+    // a heavy vertex has more than 1024 edge groups, so at most m/4096 of them,
+    // each split into chunks of 4096 groups
+    const uint64_t m = p->g->m;
+    p->ms_heavy_cap = (uint32_t)std::min<uint64_t>(m / 4096 + m / 16384 + 1024, 0xFFFFFFFFull);
+    RC(grow_buffer(p, (void**)&p->ms_heavy, 0, (size_t)p->ms_heavy_cap * sizeof(uint4), 0));
+    RC(grow_buffer(p, (void**)&p->ms_c, 0, sizeof(MsCounters), 0));
+    RC(grow_buffer(p, (void**)&p->ms_sets, 0, MS_SETS * 4, 0));
+    RC(grow_buffer(p, (void**)&p->ms_rowoff, 0, MS_SETS * 8, 0));
+    return HBX_OK;
+}
+
+// Sample the listed IC sets (ids on the host) MS_SETS at a time with the
+// bit-parallel search.  Dense sets are stored as bitmap rows (MODE_ENCODE) or
+// counted (MODE_HIST); the others are returned in `rest` for the per-set block
+// kernel, which encodes them.
+static int run_multi_source(hbx_pool* p, uint32_t mode, uint32_t cut, const std::vector<uint32_t>& ids,
+                            std::vector<uint32_t>& rest, bool timed) {
+    hbx_ctx* ctx = p->ctx;
+    RC(ensure_ms_scratch(p));
+    const uint64_t row = p->bp_words;
+    const uint32_t n = p->g->n;
+    for (size_t b0 = 0; b0 < ids.size(); b0 += MS_SETS) {
+        const uint32_t nb = (uint32_t)std::min<size_t>(MS_SETS, ids.size() - b0);
+        CK(cudaMemcpyAsync(p->ms_sets, ids.data() + b0, (size_t)nb * 4, cudaMemcpyHostToDevice, p->stream));
+        CK(cudaMemsetAsync(p->ms_c, 0, sizeof(MsCounters), p->stream));
+        MsArgs a;
+        memset(&a, 0, sizeof(a));
+        a.g = dev_graph(p->g);
+        a.key0 = (uint32_t)p->seed;
+        a.key1 = (uint32_t)(p->seed >> 32);
+        a.epoch = p->o.pool_epoch;
+        a.sets = p->ms_sets;
+        a.nsets = nb;
+        a.vis = p->ms_vis;
+        a.cur = p->ms_cur;
+        a.nxt = p->ms_nxt;
+        a.F = p->ms_F;
+        a.N = p->ms_N;
+        a.heavy = p->ms_heavy;
+        a.heavy_cap = p->ms_heavy_cap;
+        a.mc = p->ms_c;
+        a.ctr = p->ctr;
+        a.recs = p->recs;
+        a.rowoff = p->ms_rowoff;
+        if (timed) CK(cudaEventRecord(p->ev0, p->stream));
+        CK(launch_ms_start(a, p->stream));
+        p->launches++;
+        for (uint64_t level = 0;; level++) {
+            if (level > (uint64_t)n) return fail(ctx, HBX_ERR_INTERNAL, "bit-parallel search did not end");
+            CK(launch_ms_level(a, ctx->sms, p->stream));
+            p->launches += 3;
+            std::swap(a.cur, a.nxt);
+            std::swap(a.F, a.N);
+            uint32_t nF = 0;
+            CK(cudaMemcpyAsync(&nF, &p->ms_c->nF, 4, cudaMemcpyDeviceToHost, p->stream));
+            CK(cudaStreamSynchronize(p->stream));
+            if (nF == 0) break;
+        }
+        CK(launch_ms_finish(a, ctx->sms, p->stream));
+        p->launches++;
+        MsCounters mc;
+        CK(cudaMemcpyAsync(&mc, p->ms_c, sizeof(mc), cudaMemcpyDeviceToHost, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+        uint32_t dense = 0, nd = 0;
+        unsigned long long rowoff[MS_SETS] = {0};
+        for (uint32_t s = 0; s < nb; s++) {
+            if ((unsigned long long)cut * mc.size[s] > n) {
+                dense |= 1u << s;
+                rowoff[s] = p->hc.bm_cursor + (unsigned long long)nd * row;
+                nd++;
+            } else {
+                rest.push_back(ids[b0 + s]);
+            }
+        }
+        if (mode == MODE_ENCODE && nd) {
+            // the rows are placed by the host: no set of the batch can overflow
+            const unsigned long long cursor = p->hc.bm_cursor + (unsigned long long)nd * row;
+            RC(grow_heap(p, p->bm, cursor));
+            CK(cudaMemcpyAsync(p->ms_rowoff, rowoff, sizeof(rowoff), cudaMemcpyHostToDevice, p->stream));
+            CK(cudaMemcpyAsync(&p->ctr->bm_cursor, &cursor, 8, cudaMemcpyHostToDevice, p->stream));
+            p->hc.bm_cursor = cursor;
+        }
+        CK(launch_ms_emit(a, dense, mode, row, p->bm.d, ctx->sms, p->stream));
+        p->launches += 2;
+        if (timed) {
+            CK(cudaEventRecord(p->ev1, p->stream));
+            CK(cudaEventSynchronize(p->ev1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+            p->sample_kernel_s += ms * 1e-3;
+            p->sample_kernel_launches++;
+        }
+    }
+    return read_counters(p);
+}
+
 // Sample sets (range [j0, j0+count) or list) in `mode`, handling sets too large
 // for a warp and heaps that run out.  The list, if any, is a device array.
 // The batched form runs the persistent warp kernel, then the shared-memory
@@ -518,9 +624,21 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
             RC(timed_launch(p, timed, [&] { return launch_sample_warp(a, sh.qw, ctx->sms, p->stream); }));
             const uint32_t nmid = (uint32_t)p->hc.big_count;
             if (nmid) RC(timed_launch(p, timed, [&] { return launch_sample_mid(a, nmid, ctx->sms, p->stream); }));
-            const uint32_t nbig = (uint32_t)p->hc.giant_count;
+            uint32_t nbig = (uint32_t)p->hc.giant_count;
+            if (nbig && p->model == HBX_IC && mode != MODE_RAW) {
+                // IC sets that outgrew shared memory: bit-parallel search, 32 at a
+                // time; those below the density cut go on to the block kernel
+                std::vector<uint32_t> ids(nbig), rest;
+                CK(cudaMemcpyAsync(ids.data(), p->giant_list, (size_t)nbig * 4, cudaMemcpyDeviceToHost, p->stream));
+                CK(cudaStreamSynchronize(p->stream));
+                RC(run_multi_source(p, mode, cut, ids, rest, timed));
+                nbig = (uint32_t)rest.size();
+                if (nbig)
+                    CK(cudaMemcpyAsync(p->giant_list, rest.data(), (size_t)nbig * 4, cudaMemcpyHostToDevice,
+                                       p->stream));
+            }
             if (nbig) {
-                SampleArgs b = a;
+                SampleArgs b = sample_args(p, mode, j0, count, list, freq, cut, sh);  // heaps may have moved
                 b.big_list = p->giant_list;
                 RC(run_block_path(p, b, nbig, sh.bc ? sh.bc : 1u, timed));
             }
@@ -1121,7 +1239,8 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
                     p->code_of_rank, p->len_of_rank, p->lut, p->dec, p->items, p->bm_sets, p->big_list,
                     p->retry_list, p->list_in, p->giant_list, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
                     p->alive, p->cov_huff, p->cov_bm, p->cov_raw, p->st, p->partials, p->ticket, p->d_seeds,
-                    p->d_marg, p->dec_items, p->cnt_base};
+                    p->d_marg, p->dec_items, p->cnt_base, p->ms_vis, p->ms_cur, p->ms_nxt, p->ms_F, p->ms_N,
+                    p->ms_heavy, p->ms_c, p->ms_sets, p->ms_rowoff};
     for (void* b : bufs) dfree(c, b);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);

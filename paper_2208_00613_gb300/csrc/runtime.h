@@ -96,6 +96,13 @@ struct hbx_pool {
     uint32_t *bp_visited = nullptr, *bp_rbits = nullptr, *bp_aux = nullptr, *bp_queue = nullptr;
     uint32_t bp_slots = 0;
     uint64_t bp_words = 0;
+    // bit-parallel search scratch (masks and lists of n entries each)
+    uint32_t *ms_vis = nullptr, *ms_cur = nullptr, *ms_nxt = nullptr, *ms_F = nullptr, *ms_N = nullptr;
+    uint4* ms_heavy = nullptr;
+    uint32_t ms_heavy_cap = 0;
+    hbx::MsCounters* ms_c = nullptr;
+    uint32_t* ms_sets = nullptr;
+    unsigned long long* ms_rowoff = nullptr;
     // selection state
     int32_t* cnt = nullptr;
     // counts of sets [0, base_T) before any decrement, kept for the next

@@ -57,7 +57,6 @@ struct WarpLocal {
     uint32_t stage[40];
 };
 
-__device__ __forceinline__ void set_error(Counters* c, unsigned long long code) { atomicMax(&c->error, code); }
 
 // Open-addressing insert into a warp's shared hash set (key v+1, 0 = empty).
 // The table holds at most QW + 31 keys in 2*QW slots, so a probe always ends.
@@ -75,7 +74,6 @@ __device__ __forceinline__ bool hash_insert(uint32_t* h, uint32_t mask, uint32_t
     return false;
 }
 
-__device__ __forceinline__ bool ic_live(uint32_t x, float p) { return (float)(x >> 8) * 0x1p-24f < p; }
 
 // Coins of one aligned 4-edge group gg of set j, restricted to [eb, ee).
 // Returns the live mask; adds the in-range edge count to *scanned.
@@ -941,7 +939,7 @@ __global__ void __launch_bounds__(BP_THREADS, 2) sample_block_kernel(SampleArgs 
         const int failed = *fail0;
         if (crank == 0 && tid == 0) {
             if (failed) a.retry_list[atomicAdd(&a.ctr->retry_count, 1ull)] = j;
-            else atomicAdd(&a.ctr->sets_big, 1ull);
+            else if (a.mode != MODE_HIST) atomicAdd(&a.ctr->sets_big, 1ull);
         }
         if (!failed) {
             scanned += set_scanned;
@@ -1372,7 +1370,7 @@ __global__ void __launch_bounds__(BP_THREADS) sample_mid_kernel(SampleArgs a, ui
         const bool failed = s.fail != 0;
         if (tid == 0 && !overflow) {
             if (failed) a.retry_list[atomicAdd(&a.ctr->retry_count, 1ull)] = j;
-            else atomicAdd(&a.ctr->sets_big, 1ull);
+            else if (a.mode != MODE_HIST) atomicAdd(&a.ctr->sets_big, 1ull);
         }
         if (!overflow && !failed) {
             scanned += set_scanned;

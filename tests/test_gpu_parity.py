@@ -165,6 +165,38 @@ def test_encoded_sets_wc_1m(ctx):
     hbx.hbx_graph_destroy(G)
 
 
+@pytest.mark.parametrize("cut", [32, 2])
+def test_giant_ic_sets_bit_parallel(ctx, cut):
+    """Supercritical IC (mean live in-degree 2): many sets outgrow shared memory
+    and are searched 32 at a time.  cut 32 makes them bitmaps; cut 2 leaves the
+    ones under n/2 vertices to the per-set block kernel (Huffman).  Sets, their
+    encodings, the warm-up frequencies and the edge counts equal the oracle's."""
+    g = synth.rmat(1 << 15, 1 << 19, 41)
+    g.prob = synth.ic_uniform(g, 41, 0.25)
+    G = hbx.hbx_graph_create(ctx, g)
+    T, W = 700, 150
+    p = hbx.hbx_pool_create(ctx, G, "IC", 13, opts(encode=1, warmup_sets=W, density_cut=cut))
+    hbx.hbx_pool_extend(ctx, p, T)
+    op = oracle.Pool(g, oracle.IC, 13)
+    op.extend(T)
+    sizes = op.sizes()
+    assert (sizes > 4096).sum() > 64  # several batches of the bit-parallel search
+    assert_same_sets(gpu_sets(ctx, p, 0, T), oracle_sets(op, 0, T))
+    _check_encoded(ctx, p, op, g, W, cut, T, sample=range(0, T, 5))
+    st = hbx.hbx_pool_stats(ctx, p)
+    sc, lv = op.edge_counts()
+    assert st["edges_scanned"] == sc and st["edges_live"] == lv
+    assert st["rr_vertices"] == int(sizes.sum())
+    assert st["sets_bitmap"] == int((cut * sizes > g.n).sum())
+    if cut == 2:
+        assert ((sizes > 4096) & (cut * sizes <= g.n)).sum() > 0  # some went on to the block kernel
+    s, m, c = hbx.hbx_pool_select(ctx, p, T, 20)
+    so, mo, co = op.greedy(T, 20)
+    assert s.tolist() == so.tolist() and m.tolist() == mo.tolist() and c == co
+    hbx.hbx_pool_destroy(p)
+    hbx.hbx_graph_destroy(G)
+
+
 @pytest.mark.parametrize("qw", [64, 256])
 def test_lt_sets(ctx, qw):
     g = synth.rmat(1 << 16, 1 << 20, 33)
