@@ -18,7 +18,7 @@ int block_path_max_clusters(uint32_t csize);
 constexpr uint32_t MS_SETS = 32;  // sets searched together, one mask bit each
 
 struct MsCounters {
-    uint32_t nF, nN, nH, pad;         // frontier, next frontier, heavy chunks of this level
+    uint32_t nF, nN, nH, pad;         // frontier, next frontier being compacted, heavy chunks of this level
     unsigned long long size[MS_SETS];     // per set of the batch
     unsigned long long scanned[MS_SETS];
     unsigned long long live[MS_SETS];
@@ -30,10 +30,9 @@ struct MsArgs {
     const uint32_t* sets;  // [nsets] set ids of the batch
     uint32_t nsets;
     uint32_t* vis;         // [n] masks: visited
-    uint32_t* cur;         // [n] masks: this level's frontier (cleared as read)
-    uint32_t* nxt;         // [n] masks: next level's frontier
-    uint32_t* F;           // [n] this level's frontier vertices
-    uint32_t* N;           // [n] next level's frontier vertices
+    uint32_t* nxt;         // [n] masks: reached during this level
+    uint32_t* F;           // [n] frontier vertices
+    uint32_t* Ff;          // [n] their masks: the sets whose frontier holds them
     uint4* heavy;          // (vertex, first group, end group, mask) chunks of this level's heavy vertices
     uint32_t heavy_cap;
     MsCounters* mc;
@@ -42,14 +41,20 @@ struct MsArgs {
     const unsigned long long* rowoff;  // [MS_SETS] bitmap-heap word offset of each dense set's row
 };
 
-cudaError_t launch_ms_start(const MsArgs& a, cudaStream_t s);
-// one level: light and heavy expansion, then the next list becomes the frontier
+// roots of the batch, compacted into the first frontier
+cudaError_t launch_ms_start(const MsArgs& a, int sms, cudaStream_t s);
+// one level: light and heavy expansion, then compaction into the next frontier
 cudaError_t launch_ms_level(const MsArgs& a, int sms, cudaStream_t s);
 // per-set sizes and scanned edges into a.mc
 cudaError_t launch_ms_finish(const MsArgs& a, int sms, cudaStream_t s);
 // bitmap rows and records of the dense sets; masks cleared
 cudaError_t launch_ms_emit(const MsArgs& a, uint32_t dense, uint32_t mode, uint64_t row_words, uint32_t* bm_heap,
                            int sms, cudaStream_t s);
+
+// sets of a bit-parallel batch under the density cut, encoded one block each
+// (scratch slot b for the b-th listed set)
+cudaError_t launch_ms_sparse(const SampleArgs& a, const uint32_t* vis, const uint32_t* sbits, const uint32_t* ids,
+                             const MsCounters* mc, uint32_t count, cudaStream_t s);
 
 // ---- selection (select.cu) ----
 struct SelState {

@@ -4,21 +4,24 @@
 // reach its root through edges whose coin, drawn from Philox at (edge group,
 // j, epoch, 1), is live.  The set does not depend on the order in which the
 // search visits vertices, so up to 32 such sets are searched together, one
-// bit per set: vis[v], cur[v] and nxt[v] are 32-bit masks (visited, this
-// level's frontier, next level's frontier), and a vertex is expanded once per
-// level for every set whose frontier holds it.  Its in-edge probabilities and
-// sources are then read once for all of those sets, and each set still draws
-// its own coin for every in-edge of every vertex it visits, so the sets, their
-// scanned and live edge counts are those of one search per set.
+// bit per set: vis[v] and nxt[v] are 32-bit masks (visited; reached during
+// this level), and the frontier lists each vertex once per level with the
+// mask of the sets whose frontier holds it.  A vertex's in-edge probabilities
+// and sources are then read once for all of those sets, and each set still
+// draws its own coin for every in-edge of every vertex it visits, so the sets
+// and their scanned and live edge counts are those of one search per set.
 //
-// A level is two launches: the light kernel takes the frontier list 32
-// vertices per warp (edge groups spread over the lanes by a warp prefix sum)
-// and moves vertices with more than MS_HEAVY groups to a list of chunks of
-// MS_CHUNK groups, which the heavy kernel then spreads over whole blocks.
-// The host advances levels until the frontier is empty, then a tally pass
-// gives each set's size and scanned edges, and the emit pass writes the
-// dense sets' bitmap rows (a 32 x 32 bit transpose per warp through shared
-// memory) and clears the masks for the next batch.
+// A level is: the light kernel takes the frontier 32 vertices per warp (edge
+// groups spread over the lanes by a warp prefix sum; vertices with more than
+// MS_HEAVY groups are cut into chunks of MS_CHUNK groups for the heavy
+// kernel, which spreads them over whole blocks); every live edge ORs its sets
+// into nxt[source] with a reduction that returns nothing, so no thread waits
+// on it; then the compaction pass turns nxt into the next frontier, keeping
+// for each vertex only the sets that had not visited it yet (marking them in
+// vis), and clears nxt.  The host advances levels until the frontier is empty,
+// then a tally pass gives each set's size and scanned edges, and the emit pass
+// writes the dense sets' bitmap rows (a 32 x 32 bit transpose per warp through
+// shared memory) and clears vis for the next batch.
 #include <cstdint>
 
 #include "common.cuh"
@@ -28,122 +31,83 @@ namespace hbx {
 
 constexpr int MS_THREADS = 256;
 constexpr int MS_WARPS = MS_THREADS / 32;
-constexpr uint32_t MS_HEAVY = 1024;  // edge groups above which a vertex is split into chunks
-constexpr uint32_t MS_CHUNK = 4096;  // edge groups per chunk of a heavy vertex
+// A warp takes 32 frontier vertices of at most MS_HEAVY edge groups each, so
+// no warp holds more than 1024 groups; bigger vertices are cut into chunks of
+// MS_CHUNK groups that whole blocks take.
+constexpr uint32_t MS_HEAVY = 32;
+constexpr uint32_t MS_CHUNK = 1024;
 
-// Live-edge counts per set are kept per lane (s_live[warp][set][lane]: every
-// lane owns a column, so the updates need no atomics and hit distinct banks)
-// and summed when the block ends.
-using LiveCounts = uint32_t[MS_WARPS][MS_SETS][32];
-
-__device__ __forceinline__ void ms_init_shared(const MsArgs& a, uint32_t* s_sets, LiveCounts& s_live) {
+// Per-warp live-edge counts of the batch's sets in shared memory, added to the
+// batch totals when the warp is done.
+__device__ __forceinline__ void ms_init_shared(const MsArgs& a, uint32_t* s_sets, uint32_t (*s_live)[MS_SETS]) {
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < MS_SETS) s_sets[threadIdx.x] = threadIdx.x < a.nsets ? a.sets[threadIdx.x] : 0u;
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (uint32_t s = 0; s < MS_SETS; s++) s_live[warp][s][lane] = 0;
+    s_live[warp][lane] = 0;
     __syncthreads();
 }
 
-__device__ __forceinline__ void ms_flush_live(const MsArgs& a, const LiveCounts& s_live) {
-    __syncthreads();
+__device__ __forceinline__ void ms_flush_live(const MsArgs& a, uint32_t (*s_live)[MS_SETS]) {
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // warp w sums sets w, w + MS_WARPS, ... over every warp's lanes
-    for (uint32_t s = warp; s < MS_SETS; s += MS_WARPS) {
-        unsigned long long t = 0;
-        for (uint32_t w = 0; w < MS_WARPS; w++) t += s_live[w][s][lane];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
-        if (lane == 0 && t) atomicAdd(&a.mc->live[s], t);
-    }
-}
-
-// Append the vertices flagged by the lanes of a warp to the next frontier
-// list (one atomic per warp).  Called by every lane of the warp.
-__device__ __forceinline__ void ms_append(const MsArgs& a, bool app, uint32_t u) {
-    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, app);
-    if (!bal) return;
-    const uint32_t lane = lane_id(), leader = __ffs(bal) - 1;
-    uint32_t pos = 0;
-    if (lane == leader) pos = atomicAdd(&a.mc->nN, (uint32_t)__popc(bal));
-    pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-    if (app) a.N[pos + __popc(bal & lanemask_lt())] = u;
+    __syncwarp();
+    const uint32_t c = s_live[warp][lane];
+    if (c) atomicAdd(&a.mc->live[lane], (unsigned long long)c);
 }
 
 // One aligned group of 4 in-edges gg of a frontier vertex whose in-edges are
-// [eb, ee), for the sets in mask f.  Every lane of the warp calls it (valid
-// false for lanes without a group).
-__device__ __forceinline__ void ms_group(const MsArgs& a, const uint32_t* s_sets, LiveCounts& s_live,
-                                         bool valid, uint32_t gg, uint32_t eb, uint32_t ee, uint32_t f) {
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// [eb, ee), for the sets in mask f.
+__device__ __forceinline__ void ms_group(const MsArgs& a, const uint32_t* s_sets, uint32_t* s_live_w, uint32_t gg,
+                                         uint32_t eb, uint32_t ee, uint32_t f) {
+    const float4 p4 = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
+    const uint32_t e0 = gg * 4u;
+    const bool v0 = e0 >= eb && e0 < ee, v1 = e0 + 1 >= eb && e0 + 1 < ee;
+    const bool v2 = e0 + 2 >= eb && e0 + 2 < ee, v3 = e0 + 3 >= eb && e0 + 3 < ee;
     uint32_t em0 = 0, em1 = 0, em2 = 0, em3 = 0;  // sets for which edge 4gg+k is live
-    if (valid) {
-        const float4 p4 = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
-        const uint32_t e0 = gg * 4u;
-        const bool v0 = e0 >= eb && e0 < ee, v1 = e0 + 1 >= eb && e0 + 1 < ee;
-        const bool v2 = e0 + 2 >= eb && e0 + 2 < ee, v3 = e0 + 3 >= eb && e0 + 3 < ee;
-        while (f) {
-            const uint32_t s = __ffs(f) - 1;
-            f &= f - 1;
-            const uint4 x = philox4x32_10(make_uint4(gg, s_sets[s], a.epoch, STREAM_IC), a.key0, a.key1);
-            const uint32_t l0 = v0 && ic_live(x.x, p4.x), l1 = v1 && ic_live(x.y, p4.y);
-            const uint32_t l2 = v2 && ic_live(x.z, p4.z), l3 = v3 && ic_live(x.w, p4.w);
-            const uint32_t nl = l0 + l1 + l2 + l3;
-            if (nl) {
-                s_live[warp][s][lane] += nl;
-                em0 |= l0 << s;
-                em1 |= l1 << s;
-                em2 |= l2 << s;
-                em3 |= l3 << s;
-            }
+    while (f) {
+        const uint32_t s = __ffs(f) - 1;
+        f &= f - 1;
+        const uint4 x = philox4x32_10(make_uint4(gg, s_sets[s], a.epoch, STREAM_IC), a.key0, a.key1);
+        const uint32_t l0 = v0 && ic_live(x.x, p4.x), l1 = v1 && ic_live(x.y, p4.y);
+        const uint32_t l2 = v2 && ic_live(x.z, p4.z), l3 = v3 && ic_live(x.w, p4.w);
+        const uint32_t nl = l0 + l1 + l2 + l3;
+        if (nl) {
+            atomicAdd(&s_live_w[s], nl);
+            em0 |= l0 << s;
+            em1 |= l1 << s;
+            em2 |= l2 << s;
+            em3 |= l3 << s;
         }
     }
-    const uint32_t em[4] = {em0, em1, em2, em3};
-    uint32_t u[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) u[k] = em[k] ? __ldg(a.g.col + gg * 4u + k) : NONE;
-    bool app[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        app[k] = false;
-        if (em[k]) {
-            const uint32_t fresh = em[k] & ~atomicOr(&a.vis[u[k]], em[k]);
-            if (fresh) app[k] = atomicOr(&a.nxt[u[k]], fresh) == 0u;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; k++) ms_append(a, app[k], u[k]);
+    if (em0) atomicOr(&a.nxt[__ldg(a.g.col + e0)], em0);
+    if (em1) atomicOr(&a.nxt[__ldg(a.g.col + e0 + 1)], em1);
+    if (em2) atomicOr(&a.nxt[__ldg(a.g.col + e0 + 2)], em2);
+    if (em3) atomicOr(&a.nxt[__ldg(a.g.col + e0 + 3)], em3);
 }
 
-// Roots of the batch's sets: visited and in the first frontier.  <<<1, 32>>>
+// Roots of the batch's sets, reached at level 0.  <<<1, 32>>>
 __global__ void ms_start_kernel(MsArgs a) {
     const uint32_t s = threadIdx.x;
-    bool app = false;
-    uint32_t root = 0;
     if (s < a.nsets) {
         const uint4 rr = philox4x32_10(make_uint4(0u, a.sets[s], a.epoch, STREAM_ROOT), a.key0, a.key1);
-        root = __umulhi(rr.x, a.g.n);
-        atomicOr(&a.vis[root], 1u << s);
-        app = atomicOr(&a.cur[root], 1u << s) == 0u;
+        atomicOr(&a.nxt[__umulhi(rr.x, a.g.n)], 1u << s);
     }
-    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, app);
-    if (app) a.F[__popc(bal & lanemask_lt())] = root;
-    if (s == 0) a.mc->nF = __popc(bal);
 }
 
-__global__ void __launch_bounds__(MS_THREADS) ms_light_kernel(MsArgs a) {
+__global__ void __launch_bounds__(MS_THREADS, 5) ms_light_kernel(MsArgs a) {
     __shared__ uint32_t s_sets[MS_SETS];
-    __shared__ LiveCounts s_live;
+    __shared__ uint32_t s_live[MS_WARPS][MS_SETS];
     __shared__ uint32_t w_scan[MS_WARPS][32], w_g0[MS_WARPS][32], w_eb[MS_WARPS][32], w_ee[MS_WARPS][32],
         w_f[MS_WARPS][32];
+    const uint32_t nF = a.mc->nF;
+    if (blockIdx.x * MS_WARPS * 32 >= nF) return;  // thin level: this block has no chunk
     ms_init_shared(a, s_sets, s_live);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t nF = a.mc->nF;
     const uint32_t stride = gridDim.x * MS_WARPS * 32;
     for (uint32_t c = (blockIdx.x * MS_WARPS + warp) * 32; c < nF; c += stride) {
         const uint32_t i = c + lane;
         uint32_t v = 0, f = 0, b = 0, e = 0, gfirst = 0, ng = 0;
         if (i < nF) {
             v = a.F[i];
-            f = a.cur[v];
-            a.cur[v] = 0u;  // cur becomes the next level's nxt and must be clear
+            f = a.Ff[i];
             b = __ldg(a.g.row_ptr + v);
             e = __ldg(a.g.row_ptr + v + 1);
             if (e > b) {
@@ -168,23 +132,15 @@ __global__ void __launch_bounds__(MS_THREADS) ms_light_kernel(MsArgs a) {
         w_ee[warp][lane] = e;
         w_f[warp][lane] = f;
         __syncwarp();
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t t = base + lane;
-            const bool valid = t < total;
-            uint32_t gg = 0, eb = 0, ee = 0, ff = 0;
-            if (valid) {
-                uint32_t lo = 0, hi = 31;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (w_scan[warp][mid] > t) hi = mid;
-                    else lo = mid + 1;
-                }
-                gg = w_g0[warp][lo] + (t - (lo ? w_scan[warp][lo - 1] : 0u));
-                eb = w_eb[warp][lo];
-                ee = w_ee[warp][lo];
-                ff = w_f[warp][lo];
+        for (uint32_t t = lane; t < total; t += 32) {
+            uint32_t lo = 0, hi = 31;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (w_scan[warp][mid] > t) hi = mid;
+                else lo = mid + 1;
             }
-            ms_group(a, s_sets, s_live, valid, gg, eb, ee, ff);
+            const uint32_t gg = w_g0[warp][lo] + (t - (lo ? w_scan[warp][lo - 1] : 0u));
+            ms_group(a, s_sets, s_live[warp], gg, w_eb[warp][lo], w_ee[warp][lo], w_f[warp][lo]);
         }
         __syncwarp();
     }
@@ -193,21 +149,60 @@ __global__ void __launch_bounds__(MS_THREADS) ms_light_kernel(MsArgs a) {
 
 __global__ void __launch_bounds__(MS_THREADS) ms_heavy_kernel(MsArgs a) {
     __shared__ uint32_t s_sets[MS_SETS];
-    __shared__ LiveCounts s_live;
-    ms_init_shared(a, s_sets, s_live);
+    __shared__ uint32_t s_live[MS_WARPS][MS_SETS];
     const uint32_t nH = min(a.mc->nH, a.heavy_cap);
+    if (blockIdx.x >= nH) return;
+    ms_init_shared(a, s_sets, s_live);
+    const uint32_t warp = threadIdx.x >> 5;
     for (uint32_t it = blockIdx.x; it < nH; it += gridDim.x) {
         const uint4 item = a.heavy[it];
         const uint32_t eb = __ldg(a.g.row_ptr + item.x), ee = __ldg(a.g.row_ptr + item.x + 1);
-        for (uint32_t g = item.y; g < item.z; g += MS_THREADS) {
-            const uint32_t gg = g + threadIdx.x;
-            ms_group(a, s_sets, s_live, gg < item.z, gg, eb, ee, item.w);
-        }
+        for (uint32_t gg = item.y + threadIdx.x; gg < item.z; gg += MS_THREADS)
+            ms_group(a, s_sets, s_live[warp], gg, eb, ee, item.w);
     }
     ms_flush_live(a, s_live);
 }
 
-// Next level: the list just filled becomes the frontier.  <<<1, 1>>>
+// The vertices reached during the level, with the sets that had not visited
+// them yet, become the next frontier (warp-aggregated appends); vis gains
+// those sets and nxt is cleared.  A thread takes 4 vertices with 16-byte
+// loads (the mask arrays are padded to a multiple of 4 entries).
+__global__ void __launch_bounds__(MS_THREADS) ms_compact_kernel(MsArgs a) {
+    const uint32_t lane = threadIdx.x & 31, n4 = (a.g.n + 3) / 4;
+    const uint32_t stride = gridDim.x * MS_THREADS;
+    uint4* nxt4 = reinterpret_cast<uint4*>(a.nxt);
+    uint4* vis4 = reinterpret_cast<uint4*>(a.vis);
+    for (uint32_t q0 = blockIdx.x * MS_THREADS + (threadIdx.x & ~31u); q0 < n4; q0 += stride) {
+        const uint32_t q = q0 + lane;
+        uint4 f = make_uint4(0, 0, 0, 0);
+        if (q < n4) {
+            const uint4 x = nxt4[q];
+            if (x.x | x.y | x.z | x.w) {
+                nxt4[q] = make_uint4(0, 0, 0, 0);
+                const uint4 old = vis4[q];
+                f = make_uint4(x.x & ~old.x, x.y & ~old.y, x.z & ~old.z, x.w & ~old.w);
+                if (f.x | f.y | f.z | f.w) vis4[q] = make_uint4(old.x | f.x, old.y | f.y, old.z | f.z, old.w | f.w);
+            }
+        }
+        const uint32_t c = (f.x != 0) + (f.y != 0) + (f.z != 0) + (f.w != 0);
+        const uint32_t incl = warp_incl_scan(c);
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (!total) continue;
+        uint32_t pos = 0;
+        if (lane == 31) pos = atomicAdd(&a.mc->nN, total);
+        pos = __shfl_sync(0xFFFFFFFFu, pos, 31) + incl - c;
+        const uint32_t fw[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (fw[k]) {
+                a.F[pos] = q * 4 + k;
+                a.Ff[pos] = fw[k];
+                pos++;
+            }
+    }
+}
+
+// Next level: the compacted list becomes the frontier.  <<<1, 1>>>
 __global__ void ms_advance_kernel(MsArgs a) {
     a.mc->nF = a.mc->nN;
     a.mc->nN = 0;
@@ -290,6 +285,10 @@ __global__ void ms_commit_kernel(MsArgs a, uint32_t dense, uint32_t mode, uint64
     if (d && mode == MODE_ENCODE) {
         a.recs[a.sets[s]] = make_rec(KIND_BITMAP, a.rowoff[s], (uint32_t)a.mc->size[s], 0);
         verts = a.mc->size[s];
+    }
+    // edges of the stored sets; a histogram pass counts those of its dense sets
+    // too (the autotuner measures the work per set by them)
+    if (d) {
         sc = a.mc->scanned[s];
         lv = a.mc->live[s];
     }
@@ -307,9 +306,9 @@ __global__ void ms_commit_kernel(MsArgs a, uint32_t dense, uint32_t mode, uint64
             atomicAdd(&a.ctr->sets_big, nd);
             atomicAdd(&a.ctr->rr_vertices, verts);
             atomicAdd(&a.ctr->words_used, nd * row_words);
-            atomicAdd(&a.ctr->edges_scanned, sc);
-            atomicAdd(&a.ctr->edges_live, lv);
         }
+        if (sc) atomicAdd(&a.ctr->edges_scanned, sc);
+        if (lv) atomicAdd(&a.ctr->edges_live, lv);
     }
 }
 
@@ -325,8 +324,10 @@ static uint32_t ms_grid(const void* kernel, int sms) {
     return (uint32_t)(sms * (per_sm > 0 ? per_sm : 1));
 }
 
-cudaError_t launch_ms_start(const MsArgs& a, cudaStream_t s) {
+cudaError_t launch_ms_start(const MsArgs& a, int sms, cudaStream_t s) {
     ms_start_kernel<<<1, 32, 0, s>>>(a);
+    ms_compact_kernel<<<(uint32_t)sms * 8, MS_THREADS, 0, s>>>(a);
+    ms_advance_kernel<<<1, 1, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -335,6 +336,7 @@ cudaError_t launch_ms_level(const MsArgs& a, int sms, cudaStream_t s) {
     static const uint32_t gh = ms_grid((const void*)ms_heavy_kernel, sms);
     ms_light_kernel<<<gl, MS_THREADS, 0, s>>>(a);
     ms_heavy_kernel<<<gh, MS_THREADS, 0, s>>>(a);
+    ms_compact_kernel<<<(uint32_t)sms * 8, MS_THREADS, 0, s>>>(a);
     ms_advance_kernel<<<1, 1, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -500,29 +500,29 @@ static int run_block_path(hbx_pool* p, SampleArgs a, uint32_t nitems, uint32_t c
 
 static int ensure_ms_scratch(hbx_pool* p) {
     if (p->ms_vis) return HBX_OK;
-    const uint64_t n4 = (uint64_t)p->g->n * 4;
+    const uint64_t n4 = (((uint64_t)p->g->n + 3) & ~3ull) * 4;  // 16-byte padded mask arrays
     RC(grow_buffer(p, (void**)&p->ms_vis, 0, n4, 0));
-    RC(grow_buffer(p, (void**)&p->ms_cur, 0, n4, 0));
     RC(grow_buffer(p, (void**)&p->ms_nxt, 0, n4, 0));
     RC(grow_buffer(p, (void**)&p->ms_F, 0, n4, 0));
     RC(grow_buffer(p, (void**)&p->ms_N, 0, n4, 0));
-    // a heavy vertex has more than 1024 edge groups, so at most m/4096 of them,
-    // each split into chunks of 4096 groups
+    // a heavy vertex has more than 32 edge groups, so at most m/128 of them,
+    // each cut into chunks of 1024 groups
     const uint64_t m = p->g->m;
-    p->ms_heavy_cap = (uint32_t)std::min<uint64_t>(m / 4096 + m / 16384 + 1024, 0xFFFFFFFFull);
+    p->ms_heavy_cap = (uint32_t)std::min<uint64_t>(m / 128 + m / 4096 + 1024, 0xFFFFFFFFull);
     RC(grow_buffer(p, (void**)&p->ms_heavy, 0, (size_t)p->ms_heavy_cap * sizeof(uint4), 0));
     RC(grow_buffer(p, (void**)&p->ms_c, 0, sizeof(MsCounters), 0));
     RC(grow_buffer(p, (void**)&p->ms_sets, 0, MS_SETS * 4, 0));
     RC(grow_buffer(p, (void**)&p->ms_rowoff, 0, MS_SETS * 8, 0));
+    RC(grow_buffer(p, (void**)&p->ms_sparse, 0, 2 * MS_SETS * 4, 0));
     return HBX_OK;
 }
 
 // Sample the listed IC sets (ids on the host) MS_SETS at a time with the
 // bit-parallel search.  Dense sets are stored as bitmap rows (MODE_ENCODE) or
-// counted (MODE_HIST); the others are returned in `rest` for the per-set block
-// kernel, which encodes them.
+// counted (MODE_HIST); each of the others is encoded (or histogrammed) by one
+// block from its membership row, as the per-set block kernel would.
 static int run_multi_source(hbx_pool* p, uint32_t mode, uint32_t cut, const std::vector<uint32_t>& ids,
-                            std::vector<uint32_t>& rest, bool timed) {
+                            uint32_t* freq, const Shape& sh, bool timed) {
     hbx_ctx* ctx = p->ctx;
     RC(ensure_ms_scratch(p));
     const uint64_t row = p->bp_words;
@@ -540,10 +540,9 @@ static int run_multi_source(hbx_pool* p, uint32_t mode, uint32_t cut, const std:
         a.sets = p->ms_sets;
         a.nsets = nb;
         a.vis = p->ms_vis;
-        a.cur = p->ms_cur;
         a.nxt = p->ms_nxt;
         a.F = p->ms_F;
-        a.N = p->ms_N;
+        a.Ff = p->ms_N;
         a.heavy = p->ms_heavy;
         a.heavy_cap = p->ms_heavy_cap;
         a.mc = p->ms_c;
@@ -551,14 +550,12 @@ static int run_multi_source(hbx_pool* p, uint32_t mode, uint32_t cut, const std:
         a.recs = p->recs;
         a.rowoff = p->ms_rowoff;
         if (timed) CK(cudaEventRecord(p->ev0, p->stream));
-        CK(launch_ms_start(a, p->stream));
-        p->launches++;
+        CK(launch_ms_start(a, ctx->sms, p->stream));
+        p->launches += 3;
         for (uint64_t level = 0;; level++) {
             if (level > (uint64_t)n) return fail(ctx, HBX_ERR_INTERNAL, "bit-parallel search did not end");
             CK(launch_ms_level(a, ctx->sms, p->stream));
-            p->launches += 3;
-            std::swap(a.cur, a.nxt);
-            std::swap(a.F, a.N);
+            p->launches += 4;
             uint32_t nF = 0;
             CK(cudaMemcpyAsync(&nF, &p->ms_c->nF, 4, cudaMemcpyDeviceToHost, p->stream));
             CK(cudaStreamSynchronize(p->stream));
@@ -569,16 +566,26 @@ static int run_multi_source(hbx_pool* p, uint32_t mode, uint32_t cut, const std:
         MsCounters mc;
         CK(cudaMemcpyAsync(&mc, p->ms_c, sizeof(mc), cudaMemcpyDeviceToHost, p->stream));
         CK(cudaStreamSynchronize(p->stream));
-        uint32_t dense = 0, nd = 0;
+        uint32_t dense = 0, nd = 0, nsp = 0;
         unsigned long long rowoff[MS_SETS] = {0};
+        uint32_t sparse[2 * MS_SETS];  // mask bits, then set ids, of the sets under the cut
         for (uint32_t s = 0; s < nb; s++) {
             if ((unsigned long long)cut * mc.size[s] > n) {
                 dense |= 1u << s;
                 rowoff[s] = p->hc.bm_cursor + (unsigned long long)nd * row;
                 nd++;
             } else {
-                rest.push_back(ids[b0 + s]);
+                sparse[nsp] = s;
+                sparse[MS_SETS + nsp] = ids[b0 + s];
+                nsp++;
             }
+        }
+        if (nsp) {
+            RC(ensure_block_scratch(p, nsp));
+            CK(cudaMemcpyAsync(p->ms_sparse, sparse, sizeof(sparse), cudaMemcpyHostToDevice, p->stream));
+            const SampleArgs sa = sample_args(p, mode, 0, 0, nullptr, freq, cut, sh);
+            CK(launch_ms_sparse(sa, p->ms_vis, p->ms_sparse, p->ms_sparse + MS_SETS, p->ms_c, nsp, p->stream));
+            p->launches++;
         }
         if (mode == MODE_ENCODE && nd) {
             // the rows are placed by the host: no set of the batch can overflow
@@ -626,16 +633,12 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
             if (nmid) RC(timed_launch(p, timed, [&] { return launch_sample_mid(a, nmid, ctx->sms, p->stream); }));
             uint32_t nbig = (uint32_t)p->hc.giant_count;
             if (nbig && p->model == HBX_IC && mode != MODE_RAW) {
-                // IC sets that outgrew shared memory: bit-parallel search, 32 at a
-                // time; those below the density cut go on to the block kernel
-                std::vector<uint32_t> ids(nbig), rest;
+                // IC sets that outgrew shared memory: bit-parallel search, 32 at a time
+                std::vector<uint32_t> ids(nbig);
                 CK(cudaMemcpyAsync(ids.data(), p->giant_list, (size_t)nbig * 4, cudaMemcpyDeviceToHost, p->stream));
                 CK(cudaStreamSynchronize(p->stream));
-                RC(run_multi_source(p, mode, cut, ids, rest, timed));
-                nbig = (uint32_t)rest.size();
-                if (nbig)
-                    CK(cudaMemcpyAsync(p->giant_list, rest.data(), (size_t)nbig * 4, cudaMemcpyHostToDevice,
-                                       p->stream));
+                RC(run_multi_source(p, mode, cut, ids, freq, sh, timed));
+                nbig = 0;
             }
             if (nbig) {
                 SampleArgs b = sample_args(p, mode, j0, count, list, freq, cut, sh);  // heaps may have moved
@@ -1239,8 +1242,8 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
                     p->code_of_rank, p->len_of_rank, p->lut, p->dec, p->items, p->bm_sets, p->big_list,
                     p->retry_list, p->list_in, p->giant_list, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
                     p->alive, p->cov_huff, p->cov_bm, p->cov_raw, p->st, p->partials, p->ticket, p->d_seeds,
-                    p->d_marg, p->dec_items, p->cnt_base, p->ms_vis, p->ms_cur, p->ms_nxt, p->ms_F, p->ms_N,
-                    p->ms_heavy, p->ms_c, p->ms_sets, p->ms_rowoff};
+                    p->d_marg, p->dec_items, p->cnt_base, p->ms_vis, p->ms_nxt, p->ms_F, p->ms_N,
+                    p->ms_heavy, p->ms_c, p->ms_sets, p->ms_rowoff, p->ms_sparse};
     for (void* b : bufs) dfree(c, b);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);

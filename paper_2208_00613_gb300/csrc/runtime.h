@@ -97,12 +97,13 @@ struct hbx_pool {
     uint32_t bp_slots = 0;
     uint64_t bp_words = 0;
     // bit-parallel search scratch (masks and lists of n entries each)
-    uint32_t *ms_vis = nullptr, *ms_cur = nullptr, *ms_nxt = nullptr, *ms_F = nullptr, *ms_N = nullptr;
+    uint32_t *ms_vis = nullptr, *ms_nxt = nullptr, *ms_F = nullptr, *ms_N = nullptr;  // ms_N: frontier masks
     uint4* ms_heavy = nullptr;
     uint32_t ms_heavy_cap = 0;
     hbx::MsCounters* ms_c = nullptr;
     uint32_t* ms_sets = nullptr;
     unsigned long long* ms_rowoff = nullptr;
+    uint32_t* ms_sparse = nullptr;  // mask bits and ids of a batch's sets under the density cut
     // selection state
     int32_t* cnt = nullptr;
     // counts of sets [0, base_T) before any decrement, kept for the next

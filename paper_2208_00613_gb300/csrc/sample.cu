@@ -703,6 +703,195 @@ __device__ void block_walk_lt(const SampleArgs& a, uint32_t j, uint32_t* visited
     __syncthreads();
 }
 
+// Encode the finished set j, whose vertices are queue[0..size) and bits in
+// visited, with the whole block: warm-up frequencies, raw ids, a bitmap row or
+// Huffman codes by the density cut.  Leaves visited and rbits clear; sets
+// s.fail when a heap ran out (nothing of the set is then recorded).
+__device__ void block_emit(const SampleArgs& a, uint32_t j, uint32_t size, uint32_t* visited, uint32_t* rbits,
+                           uint32_t* aux, uint32_t* queue, BlockShared& s) {
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t n = a.g.n;
+    bool clear_by_list = true;
+    if (a.mode == MODE_HIST) {
+        if ((unsigned long long)a.cut * size <= n) {
+            for (uint32_t i = tid; i < size; i += BP_THREADS) atomicAdd(&a.freq[queue[i]], 1u);
+            if (tid == 0) atomicAdd(&a.ctr->hist_verts, (unsigned long long)size);
+        } else if (tid == 0) {
+            atomicAdd(&a.ctr->hist_dense, 1ull);
+        }
+    } else if (a.mode == MODE_RAW) {
+        if (tid == 0) {
+            s.off = atomicAdd(&a.ctr->raw_cursor, (unsigned long long)size);
+            s.fail = s.off + size > a.raw_cap;
+            if (s.fail) atomicMin(&a.ctr->raw_fail, s.off);
+        }
+        __syncthreads();
+        if (!s.fail) {
+            for (uint32_t i = tid; i < size; i += BP_THREADS) a.raw_heap[s.off + i] = queue[i];
+            if (tid == 0) {
+                a.recs[j] = make_rec(KIND_RAW, s.off, size, 0);
+                atomicAdd(&a.ctr->sets_raw, 1ull);
+                atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                atomicAdd(&a.ctr->words_used, (unsigned long long)size);
+            }
+        }
+    } else if ((unsigned long long)a.cut * size > n) {
+        const uint64_t row = a.bp_words;  // ceil(n/32) rounded up to 4
+        if (tid == 0) {
+            s.off = atomicAdd(&a.ctr->bm_cursor, (unsigned long long)row);
+            s.fail = s.off + row > a.bm_cap;
+            if (s.fail) atomicMin(&a.ctr->bm_fail, s.off);
+        }
+        __syncthreads();
+        uint4* vis4 = reinterpret_cast<uint4*>(visited);
+        if (!s.fail) {
+            uint4* dst = reinterpret_cast<uint4*>(a.bm_heap + s.off);
+            for (uint64_t w = tid; w < row / 4; w += BP_THREADS) {
+                dst[w] = vis4[w];
+                vis4[w] = make_uint4(0, 0, 0, 0);
+            }
+            if (tid == 0) {
+                a.recs[j] = make_rec(KIND_BITMAP, s.off, size, 0);
+                atomicAdd(&a.ctr->sets_bm, 1ull);
+                atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                atomicAdd(&a.ctr->words_used, (unsigned long long)row);
+            }
+        } else {
+            for (uint64_t w = tid; w < row / 4; w += BP_THREADS) vis4[w] = make_uint4(0, 0, 0, 0);
+        }
+        clear_by_list = false;
+    } else if (size <= BP_SORT_MAX) {
+        // Huffman, small set: keys sorted in shared memory, visited cleared by list
+        uint32_t P = 2;
+        while (P < size) P <<= 1;
+        for (uint32_t i = tid; i < P; i += BP_THREADS) {
+            uint32_t key = 0xFFFFFFFFu;
+            if (i < size) {
+                const uint32_t v = queue[i];
+                const uint32_t r = __ldg(a.cb.rank_of + v);
+                key = (r != NONE) ? r : (RAW_FLAG | v);
+                visited[v >> 5] = 0u;
+            }
+            s.keys[i] = key;
+        }
+        __syncthreads();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t i = tid; i < P; i += BP_THREADS) {
+                    const uint32_t ixj = i ^ jj;
+                    if (ixj > i) {
+                        const uint32_t x = s.keys[i], y = s.keys[ixj];
+                        if ((x > y) == ((i & k) == 0)) {
+                            s.keys[i] = y;
+                            s.keys[ixj] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (warp == 0) {
+            WarpStats ws;
+            const bool ok = warp_huff_store(a, j, s.keys, size, s.stage, ws);
+            if (lane == 0) {
+                s.fail = !ok;
+                if (ok) {
+                    atomicAdd(&a.ctr->sets_huff, 1ull);
+                    atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                    atomicAdd(&a.ctr->code_bits, ws.bits);
+                    atomicAdd(&a.ctr->words_used, ws.words);
+                }
+            }
+        }
+        __syncthreads();
+        clear_by_list = false;
+    } else {
+        // Huffman, large set: ranks into the rank bitmap, coded ids out of the
+        // visited bitmap, both read back in order
+        uint32_t mine = 0;
+        for (uint32_t i = tid; i < size; i += BP_THREADS) {
+            const uint32_t v = queue[i];
+            const uint32_t r = __ldg(a.cb.rank_of + v);
+            if (r != NONE) {
+                atomicOr(&rbits[r >> 5], 1u << (r & 31));
+                atomicAnd(&visited[v >> 5], ~(1u << (v & 31)));
+                mine++;
+            }
+        }
+        const uint32_t n_coded = block_sum(mine, s.warp);  // includes barriers
+        const uint32_t got_c = compact_bits(rbits, ((uint64_t)a.cb.nsym + 31) / 32, queue, s.warp);
+        const uint32_t got_r = compact_bits(visited, ((uint64_t)n + 31) / 32, queue + n_coded, s.warp);
+        if (got_c != n_coded || got_r != size - n_coded) set_error(a.ctr, 2);
+        const uint32_t n_raw = size - n_coded;
+        const uint32_t nch = (n_coded + 31) / 32;
+        for (uint32_t c = warp; c < nch; c += BP_WARPS) {
+            const uint32_t i = c * 32 + lane;
+            const uint32_t L = i < n_coded ? (uint32_t)__ldg(a.cb.len_of_rank + queue[i]) : 0u;
+            const uint32_t sum = warp_sum(L);
+            if (lane == 0) aux[c] = sum;
+        }
+        __syncthreads();
+        // exclusive scan of chunk bit counts, in place
+        uint32_t carry = 0;
+        for (uint32_t t0 = 0; t0 < nch; t0 += BP_THREADS) {
+            const uint32_t c = t0 + tid;
+            const uint32_t x = c < nch ? aux[c] : 0u;
+            uint32_t tot;
+            const uint32_t ex = block_excl_scan(x, s.warp, tot);
+            if (c < nch) aux[c] = carry + ex;
+            carry += tot;
+        }
+        __syncthreads();
+        const uint32_t bits = carry;
+        const uint32_t nside = side_words(n_coded);
+        const unsigned long long words = (unsigned long long)nside + n_raw + (bits + 31) / 32;
+        if (tid == 0) {
+            s.off = words ? atomicAdd(&a.ctr->code_cursor, words) : 0ull;
+            s.fail = s.off + words > a.code_cap;
+            if (s.fail) atomicMin(&a.ctr->code_fail, s.off);
+        }
+        __syncthreads();
+        if (!s.fail) {
+            uint32_t* out = a.code_heap + s.off + nside + n_raw;
+            for (uint32_t c = warp; c < nch; c += BP_WARPS) {
+                const uint32_t i = c * 32 + lane;
+                uint32_t L = 0, code = 0;
+                if (i < n_coded) {
+                    const uint32_t r = queue[i];
+                    L = __ldg(a.cb.len_of_rank + r);
+                    code = __ldg(a.cb.code_of_rank + r);
+                }
+                const uint32_t incl = warp_incl_scan(L);
+                const uint32_t o = aux[c] + incl - L;
+                if (c > 0 && lane == 0) a.code_heap[s.off + c - 1] = aux[c];
+                if (L) {
+                    const uint32_t w = o >> 5, sh = o & 31u;
+                    if (sh + L <= 32) {
+                        atomicOr(&out[w], bswap32(code << (32 - sh - L)));
+                    } else {
+                        atomicOr(&out[w], bswap32(code >> (sh + L - 32)));
+                        atomicOr(&out[w + 1], bswap32(code << (64 - sh - L)));
+                    }
+                }
+            }
+            for (uint32_t i = tid; i < n_raw; i += BP_THREADS) a.code_heap[s.off + nside + i] = queue[n_coded + i];
+            if (tid == 0) {
+                a.recs[j] = make_rec(KIND_HUFF, s.off, size, n_coded);
+                atomicAdd(&a.ctr->sets_huff, 1ull);
+                atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
+                atomicAdd(&a.ctr->code_bits, (unsigned long long)bits);
+                atomicAdd(&a.ctr->words_used, words);
+            }
+        }
+        clear_by_list = false;
+    }
+    if (clear_by_list) {
+        __syncthreads();
+        for (uint32_t i = tid; i < size; i += BP_THREADS) visited[queue[i] >> 5] = 0u;
+    }
+    __syncthreads();
+}
+
 // One heavy set per thread-block cluster (a cluster of 1 is a plain block).
 // Block 0 of the cluster owns the set's bookkeeping in its shared memory, and
 // encodes the set once the cluster has finished the search.
@@ -754,187 +943,8 @@ __global__ void __launch_bounds__(BP_THREADS, 2) sample_block_kernel(SampleArgs 
         }
         if (crank == 0) {
             __syncthreads();
-        // ---- emit ----
-        bool clear_by_list = true;
-        if (a.mode == MODE_HIST) {
-            if ((unsigned long long)a.cut * size <= n) {
-                for (uint32_t i = tid; i < size; i += BP_THREADS) atomicAdd(&a.freq[queue[i]], 1u);
-                if (tid == 0) atomicAdd(&a.ctr->hist_verts, (unsigned long long)size);
-            } else if (tid == 0) {
-                atomicAdd(&a.ctr->hist_dense, 1ull);
-            }
-        } else if (a.mode == MODE_RAW) {
-            if (tid == 0) {
-                s.off = atomicAdd(&a.ctr->raw_cursor, (unsigned long long)size);
-                s.fail = s.off + size > a.raw_cap;
-                if (s.fail) atomicMin(&a.ctr->raw_fail, s.off);
-            }
-            __syncthreads();
-            if (!s.fail) {
-                for (uint32_t i = tid; i < size; i += BP_THREADS) a.raw_heap[s.off + i] = queue[i];
-                if (tid == 0) {
-                    a.recs[j] = make_rec(KIND_RAW, s.off, size, 0);
-                    atomicAdd(&a.ctr->sets_raw, 1ull);
-                    atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
-                    atomicAdd(&a.ctr->words_used, (unsigned long long)size);
-                }
-            }
-        } else if ((unsigned long long)a.cut * size > n) {
-            const uint64_t row = a.bp_words;  // ceil(n/32) rounded up to 4
-            if (tid == 0) {
-                s.off = atomicAdd(&a.ctr->bm_cursor, (unsigned long long)row);
-                s.fail = s.off + row > a.bm_cap;
-                if (s.fail) atomicMin(&a.ctr->bm_fail, s.off);
-            }
-            __syncthreads();
-            uint4* vis4 = reinterpret_cast<uint4*>(visited);
-            if (!s.fail) {
-                uint4* dst = reinterpret_cast<uint4*>(a.bm_heap + s.off);
-                for (uint64_t w = tid; w < row / 4; w += BP_THREADS) {
-                    dst[w] = vis4[w];
-                    vis4[w] = make_uint4(0, 0, 0, 0);
-                }
-                if (tid == 0) {
-                    a.recs[j] = make_rec(KIND_BITMAP, s.off, size, 0);
-                    atomicAdd(&a.ctr->sets_bm, 1ull);
-                    atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
-                    atomicAdd(&a.ctr->words_used, (unsigned long long)row);
-                }
-            } else {
-                for (uint64_t w = tid; w < row / 4; w += BP_THREADS) vis4[w] = make_uint4(0, 0, 0, 0);
-            }
-            clear_by_list = false;
-        } else if (size <= BP_SORT_MAX) {
-            // Huffman, small set: keys sorted in shared memory, visited cleared by list
-            uint32_t P = 2;
-            while (P < size) P <<= 1;
-            for (uint32_t i = tid; i < P; i += BP_THREADS) {
-                uint32_t key = 0xFFFFFFFFu;
-                if (i < size) {
-                    const uint32_t v = queue[i];
-                    const uint32_t r = __ldg(a.cb.rank_of + v);
-                    key = (r != NONE) ? r : (RAW_FLAG | v);
-                    visited[v >> 5] = 0u;
-                }
-                s.keys[i] = key;
-            }
-            __syncthreads();
-            for (uint32_t k = 2; k <= P; k <<= 1) {
-                for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
-                    for (uint32_t i = tid; i < P; i += BP_THREADS) {
-                        const uint32_t ixj = i ^ jj;
-                        if (ixj > i) {
-                            const uint32_t x = s.keys[i], y = s.keys[ixj];
-                            if ((x > y) == ((i & k) == 0)) {
-                                s.keys[i] = y;
-                                s.keys[ixj] = x;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            if (warp == 0) {
-                WarpStats ws;
-                const bool ok = warp_huff_store(a, j, s.keys, size, s.stage, ws);
-                if (lane == 0) {
-                    s.fail = !ok;
-                    if (ok) {
-                        atomicAdd(&a.ctr->sets_huff, 1ull);
-                        atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
-                        atomicAdd(&a.ctr->code_bits, ws.bits);
-                        atomicAdd(&a.ctr->words_used, ws.words);
-                    }
-                }
-            }
-            __syncthreads();
-            clear_by_list = false;
-        } else {
-            // Huffman, large set: ranks into the rank bitmap, coded ids out of the
-            // visited bitmap, both read back in order
-            uint32_t mine = 0;
-            for (uint32_t i = tid; i < size; i += BP_THREADS) {
-                const uint32_t v = queue[i];
-                const uint32_t r = __ldg(a.cb.rank_of + v);
-                if (r != NONE) {
-                    atomicOr(&rbits[r >> 5], 1u << (r & 31));
-                    atomicAnd(&visited[v >> 5], ~(1u << (v & 31)));
-                    mine++;
-                }
-            }
-            const uint32_t n_coded = block_sum(mine, s.warp);  // includes barriers
-            const uint32_t got_c = compact_bits(rbits, ((uint64_t)a.cb.nsym + 31) / 32, queue, s.warp);
-            const uint32_t got_r = compact_bits(visited, ((uint64_t)n + 31) / 32, queue + n_coded, s.warp);
-            if (got_c != n_coded || got_r != size - n_coded) set_error(a.ctr, 2);
-            const uint32_t n_raw = size - n_coded;
-            const uint32_t nch = (n_coded + 31) / 32;
-            for (uint32_t c = warp; c < nch; c += BP_WARPS) {
-                const uint32_t i = c * 32 + lane;
-                const uint32_t L = i < n_coded ? (uint32_t)__ldg(a.cb.len_of_rank + queue[i]) : 0u;
-                const uint32_t sum = warp_sum(L);
-                if (lane == 0) aux[c] = sum;
-            }
-            __syncthreads();
-            // exclusive scan of chunk bit counts, in place
-            uint32_t carry = 0;
-            for (uint32_t t0 = 0; t0 < nch; t0 += BP_THREADS) {
-                const uint32_t c = t0 + tid;
-                const uint32_t x = c < nch ? aux[c] : 0u;
-                uint32_t tot;
-                const uint32_t ex = block_excl_scan(x, s.warp, tot);
-                if (c < nch) aux[c] = carry + ex;
-                carry += tot;
-            }
-            __syncthreads();
-            const uint32_t bits = carry;
-            const uint32_t nside = side_words(n_coded);
-            const unsigned long long words = (unsigned long long)nside + n_raw + (bits + 31) / 32;
-            if (tid == 0) {
-                s.off = words ? atomicAdd(&a.ctr->code_cursor, words) : 0ull;
-                s.fail = s.off + words > a.code_cap;
-                if (s.fail) atomicMin(&a.ctr->code_fail, s.off);
-            }
-            __syncthreads();
-            if (!s.fail) {
-                uint32_t* out = a.code_heap + s.off + nside + n_raw;
-                for (uint32_t c = warp; c < nch; c += BP_WARPS) {
-                    const uint32_t i = c * 32 + lane;
-                    uint32_t L = 0, code = 0;
-                    if (i < n_coded) {
-                        const uint32_t r = queue[i];
-                        L = __ldg(a.cb.len_of_rank + r);
-                        code = __ldg(a.cb.code_of_rank + r);
-                    }
-                    const uint32_t incl = warp_incl_scan(L);
-                    const uint32_t o = aux[c] + incl - L;
-                    if (c > 0 && lane == 0) a.code_heap[s.off + c - 1] = aux[c];
-                    if (L) {
-                        const uint32_t w = o >> 5, sh = o & 31u;
-                        if (sh + L <= 32) {
-                            atomicOr(&out[w], bswap32(code << (32 - sh - L)));
-                        } else {
-                            atomicOr(&out[w], bswap32(code >> (sh + L - 32)));
-                            atomicOr(&out[w + 1], bswap32(code << (64 - sh - L)));
-                        }
-                    }
-                }
-                for (uint32_t i = tid; i < n_raw; i += BP_THREADS) a.code_heap[s.off + nside + i] = queue[n_coded + i];
-                if (tid == 0) {
-                    a.recs[j] = make_rec(KIND_HUFF, s.off, size, n_coded);
-                    atomicAdd(&a.ctr->sets_huff, 1ull);
-                    atomicAdd(&a.ctr->rr_vertices, (unsigned long long)size);
-                    atomicAdd(&a.ctr->code_bits, (unsigned long long)bits);
-                    atomicAdd(&a.ctr->words_used, words);
-                }
-            }
-            clear_by_list = false;
+            block_emit(a, j, size, visited, rbits, aux, queue, s);
         }
-        if (clear_by_list) {
-            __syncthreads();
-            for (uint32_t i = tid; i < size; i += BP_THREADS) visited[queue[i] >> 5] = 0u;
-        }
-        __syncthreads();
-        }  // block 0 encodes
         cl.sync();  // the set is encoded and the slot is clean
         const int failed = *fail0;
         if (crank == 0 && tid == 0) {
@@ -956,6 +966,47 @@ __global__ void __launch_bounds__(BP_THREADS, 2) sample_block_kernel(SampleArgs 
     if (lane == 0) {
         if (sc) atomicAdd(&a.ctr->edges_scanned, sc);
         if (lv) atomicAdd(&a.ctr->edges_live, lv);
+    }
+}
+
+// Sets found by the bit-parallel search (msbfs.cu) that fall under the density
+// cut: block b takes mask bit sbits[b] (set ids[b]), gathers the set's
+// membership row from the masks into its scratch slot with one ballot per
+// word, lists the ids in ascending order, and encodes the set as the block
+// kernel does.  The set's size and edge counts come from the search.
+__global__ void __launch_bounds__(BP_THREADS, 2) sample_ms_sparse_kernel(SampleArgs a, const uint32_t* vis,
+                                                                        const uint32_t* sbits, const uint32_t* ids,
+                                                                        const MsCounters* mc) {
+    __shared__ BlockShared s;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t n = a.g.n, nw = (n + 31) / 32;
+    const uint32_t slot = blockIdx.x;
+    uint32_t* visited = a.bp_visited + (uint64_t)slot * a.bp_words;
+    uint32_t* rbits = a.bp_rbits + (uint64_t)slot * a.bp_words;
+    uint32_t* aux = a.bp_aux + (uint64_t)slot * a.bp_words;
+    uint32_t* queue = a.bp_queue + (uint64_t)slot * n;
+    const uint32_t sb = sbits[blockIdx.x], j = ids[blockIdx.x];
+    for (uint32_t w = warp; w < nw; w += BP_WARPS) {
+        const uint32_t v = w * 32 + lane;
+        const uint32_t m = v < n ? vis[v] : 0u;
+        const uint32_t r = __ballot_sync(0xFFFFFFFFu, (m >> sb) & 1u);
+        if (lane == 0) visited[w] = r;
+    }
+    __syncthreads();
+    const uint32_t size = compact_bits(visited, nw, queue, s.warp);  // clears visited
+    if (size != (uint32_t)mc->size[sb]) set_error(a.ctr, 6);
+    for (uint32_t i = tid; i < size; i += BP_THREADS) atomicOr(&visited[queue[i] >> 5], 1u << (queue[i] & 31));
+    if (tid == 0) s.fail = 0;
+    __syncthreads();
+    block_emit(a, j, size, visited, rbits, aux, queue, s);
+    if (tid == 0) {
+        if (s.fail) {
+            a.retry_list[atomicAdd(&a.ctr->retry_count, 1ull)] = j;
+        } else {
+            if (a.mode != MODE_HIST) atomicAdd(&a.ctr->sets_big, 1ull);
+            atomicAdd(&a.ctr->edges_scanned, mc->scanned[sb]);
+            atomicAdd(&a.ctr->edges_live, mc->live[sb]);
+        }
     }
 }
 
@@ -1435,6 +1486,13 @@ cudaError_t launch_sample_warp(const SampleArgs& a, uint32_t qw, int sms, cudaSt
 }
 
 // `slots` clusters of `csize` blocks each
+cudaError_t launch_ms_sparse(const SampleArgs& a, const uint32_t* vis, const uint32_t* sbits, const uint32_t* ids,
+                             const MsCounters* mc, uint32_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    sample_ms_sparse_kernel<<<count, BP_THREADS, 0, s>>>(a, vis, sbits, ids, mc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sample_block(const SampleArgs& a, uint32_t nbig, uint32_t slots, uint32_t csize, cudaStream_t s) {
     if (nbig == 0 || slots == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};

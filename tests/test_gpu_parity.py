@@ -168,9 +168,10 @@ def test_encoded_sets_wc_1m(ctx):
 @pytest.mark.parametrize("cut", [32, 2])
 def test_giant_ic_sets_bit_parallel(ctx, cut):
     """Supercritical IC (mean live in-degree 2): many sets outgrow shared memory
-    and are searched 32 at a time.  cut 32 makes them bitmaps; cut 2 leaves the
-    ones under n/2 vertices to the per-set block kernel (Huffman).  Sets, their
-    encodings, the warm-up frequencies and the edge counts equal the oracle's."""
+    and are searched 32 at a time.  cut 32 makes them bitmaps; with cut 2 the
+    ones under n/2 vertices are Huffman-coded from their membership rows.  Sets,
+    their encodings, the warm-up frequencies and the edge counts equal the
+    oracle's."""
     g = synth.rmat(1 << 15, 1 << 19, 41)
     g.prob = synth.ic_uniform(g, 41, 0.25)
     G = hbx.hbx_graph_create(ctx, g)
@@ -189,7 +190,7 @@ def test_giant_ic_sets_bit_parallel(ctx, cut):
     assert st["rr_vertices"] == int(sizes.sum())
     assert st["sets_bitmap"] == int((cut * sizes > g.n).sum())
     if cut == 2:
-        assert ((sizes > 4096) & (cut * sizes <= g.n)).sum() > 0  # some went on to the block kernel
+        assert ((sizes > 4096) & (cut * sizes <= g.n)).sum() > 0  # some were Huffman-coded
     s, m, c = hbx.hbx_pool_select(ctx, p, T, 20)
     so, mo, co = op.greedy(T, 20)
     assert s.tolist() == so.tolist() and m.tolist() == mo.tolist() and c == co
