@@ -18,7 +18,8 @@ int block_path_max_clusters(uint32_t csize);
 constexpr uint32_t MS_SETS = 32;  // sets searched together, one mask bit each
 
 struct MsCounters {
-    uint32_t nF, nN, nH, pad;         // frontier, next frontier being compacted, heavy chunks of this level
+    uint32_t nF, nN, nH, nsets;       // frontier, next frontier being compacted, heavy chunks of this level;
+                                      // sets of the batch
     unsigned long long size[MS_SETS];     // per set of the batch
     unsigned long long scanned[MS_SETS];
     unsigned long long live[MS_SETS];
@@ -26,9 +27,9 @@ struct MsCounters {
 
 struct MsArgs {
     DevGraph g;
+    const uint32_t* col4;  // g.col padded to 4*ceil(m/4) entries, 16-byte aligned
     uint32_t key0, key1, epoch;
-    const uint32_t* sets;  // [nsets] set ids of the batch
-    uint32_t nsets;
+    const uint32_t* sets;  // [MS_SETS] set ids of the batch (mc->nsets of them)
     uint32_t* vis;         // [n] masks: visited
     uint32_t* nxt;         // [n] masks: reached during this level
     uint32_t* F;           // [n] frontier vertices
@@ -44,7 +45,10 @@ struct MsArgs {
 // roots of the batch, compacted into the first frontier
 cudaError_t launch_ms_start(const MsArgs& a, int sms, cudaStream_t s);
 // one level: light and heavy expansion, then compaction into the next frontier
+// (every kernel returns at once when the frontier is empty, so a fixed run of
+// levels can be captured in a CUDA graph)
 cudaError_t launch_ms_level(const MsArgs& a, int sms, cudaStream_t s);
+constexpr int MS_GRAPH_LEVELS = 8;  // levels per graph launch
 // per-set sizes and scanned edges into a.mc
 cudaError_t launch_ms_finish(const MsArgs& a, int sms, cudaStream_t s);
 // bitmap rows and records of the dense sets; masks cleared

@@ -41,7 +41,7 @@ constexpr uint32_t MS_CHUNK = 1024;
 // batch totals when the warp is done.
 __device__ __forceinline__ void ms_init_shared(const MsArgs& a, uint32_t* s_sets, uint32_t (*s_live)[MS_SETS]) {
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < MS_SETS) s_sets[threadIdx.x] = threadIdx.x < a.nsets ? a.sets[threadIdx.x] : 0u;
+    if (threadIdx.x < MS_SETS) s_sets[threadIdx.x] = a.sets[threadIdx.x];  // unused slots never get a bit
     s_live[warp][lane] = 0;
     __syncthreads();
 }
@@ -53,46 +53,74 @@ __device__ __forceinline__ void ms_flush_live(const MsArgs& a, uint32_t (*s_live
     if (c) atomicAdd(&a.mc->live[lane], (unsigned long long)c);
 }
 
-// One aligned group of 4 in-edges gg of a frontier vertex whose in-edges are
-// [eb, ee), for the sets in mask f.
-__device__ __forceinline__ void ms_group(const MsArgs& a, const uint32_t* s_sets, uint32_t* s_live_w, uint32_t gg,
-                                         uint32_t eb, uint32_t ee, uint32_t f) {
-    const float4 p4 = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
+// The probabilities and sources of one aligned group of 4 in-edges.
+struct MsGroupData {
+    float4 p;
+    uint4 c;
+};
+
+__device__ __forceinline__ MsGroupData ms_load(const MsArgs& a, uint32_t gg) {
+    MsGroupData d;
+    d.p = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
+    d.c = __ldg(reinterpret_cast<const uint4*>(a.col4) + gg);
+    return d;
+}
+
+// Coins of set s on group gg: bit k of the result is edge 4gg+k's.
+__device__ __forceinline__ uint32_t ms_coins(const MsArgs& a, const MsGroupData& d, uint32_t gg, uint32_t j,
+                                             uint32_t vm) {
+    const uint4 x = philox4x32_10(make_uint4(gg, j, a.epoch, STREAM_IC), a.key0, a.key1);
+    return vm & ((uint32_t)ic_live(x.x, d.p.x) | ((uint32_t)ic_live(x.y, d.p.y) << 1) |
+                 ((uint32_t)ic_live(x.z, d.p.z) << 2) | ((uint32_t)ic_live(x.w, d.p.w) << 3));
+}
+
+// Group gg of a frontier vertex whose in-edges are [eb, ee), for the sets in
+// mask f (two sets' Philox blocks at a time, which are independent); each
+// live edge ORs its sets into nxt[source] with one reduction.
+__device__ __forceinline__ void ms_group(const MsArgs& a, const uint32_t* s_sets, uint32_t* s_live_w,
+                                         const MsGroupData& d, uint32_t gg, uint32_t eb, uint32_t ee, uint32_t f) {
     const uint32_t e0 = gg * 4u;
-    const bool v0 = e0 >= eb && e0 < ee, v1 = e0 + 1 >= eb && e0 + 1 < ee;
-    const bool v2 = e0 + 2 >= eb && e0 + 2 < ee, v3 = e0 + 3 >= eb && e0 + 3 < ee;
+    const uint32_t vm = (uint32_t)(e0 >= eb && e0 < ee) | ((uint32_t)(e0 + 1 >= eb && e0 + 1 < ee) << 1) |
+                        ((uint32_t)(e0 + 2 >= eb && e0 + 2 < ee) << 2) | ((uint32_t)(e0 + 3 >= eb && e0 + 3 < ee) << 3);
     uint32_t em0 = 0, em1 = 0, em2 = 0, em3 = 0;  // sets for which edge 4gg+k is live
     while (f) {
-        const uint32_t s = __ffs(f) - 1;
+        const uint32_t s1 = __ffs(f) - 1;
         f &= f - 1;
-        const uint4 x = philox4x32_10(make_uint4(gg, s_sets[s], a.epoch, STREAM_IC), a.key0, a.key1);
-        const uint32_t l0 = v0 && ic_live(x.x, p4.x), l1 = v1 && ic_live(x.y, p4.y);
-        const uint32_t l2 = v2 && ic_live(x.z, p4.z), l3 = v3 && ic_live(x.w, p4.w);
-        const uint32_t nl = l0 + l1 + l2 + l3;
-        if (nl) {
-            atomicAdd(&s_live_w[s], nl);
-            em0 |= l0 << s;
-            em1 |= l1 << s;
-            em2 |= l2 << s;
-            em3 |= l3 << s;
+        const uint32_t s2 = f ? __ffs(f) - 1 : s1;
+        f &= f - 1;
+        const uint32_t c1 = ms_coins(a, d, gg, s_sets[s1], vm);
+        const uint32_t c2 = s2 != s1 ? ms_coins(a, d, gg, s_sets[s2], vm) : 0u;
+        if (c1) {
+            atomicAdd(&s_live_w[s1], (uint32_t)__popc(c1));
+            em0 |= (c1 & 1u) << s1;
+            em1 |= ((c1 >> 1) & 1u) << s1;
+            em2 |= ((c1 >> 2) & 1u) << s1;
+            em3 |= ((c1 >> 3) & 1u) << s1;
+        }
+        if (c2) {
+            atomicAdd(&s_live_w[s2], (uint32_t)__popc(c2));
+            em0 |= (c2 & 1u) << s2;
+            em1 |= ((c2 >> 1) & 1u) << s2;
+            em2 |= ((c2 >> 2) & 1u) << s2;
+            em3 |= ((c2 >> 3) & 1u) << s2;
         }
     }
-    if (em0) atomicOr(&a.nxt[__ldg(a.g.col + e0)], em0);
-    if (em1) atomicOr(&a.nxt[__ldg(a.g.col + e0 + 1)], em1);
-    if (em2) atomicOr(&a.nxt[__ldg(a.g.col + e0 + 2)], em2);
-    if (em3) atomicOr(&a.nxt[__ldg(a.g.col + e0 + 3)], em3);
+    if (em0) atomicOr(&a.nxt[d.c.x], em0);
+    if (em1) atomicOr(&a.nxt[d.c.y], em1);
+    if (em2) atomicOr(&a.nxt[d.c.z], em2);
+    if (em3) atomicOr(&a.nxt[d.c.w], em3);
 }
 
 // Roots of the batch's sets, reached at level 0.  <<<1, 32>>>
 __global__ void ms_start_kernel(MsArgs a) {
     const uint32_t s = threadIdx.x;
-    if (s < a.nsets) {
+    if (s < a.mc->nsets) {
         const uint4 rr = philox4x32_10(make_uint4(0u, a.sets[s], a.epoch, STREAM_ROOT), a.key0, a.key1);
         atomicOr(&a.nxt[__umulhi(rr.x, a.g.n)], 1u << s);
     }
 }
 
-__global__ void __launch_bounds__(MS_THREADS, 5) ms_light_kernel(MsArgs a) {
+__global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
     __shared__ uint32_t s_sets[MS_SETS];
     __shared__ uint32_t s_live[MS_WARPS][MS_SETS];
     __shared__ uint32_t w_scan[MS_WARPS][32], w_g0[MS_WARPS][32], w_eb[MS_WARPS][32], w_ee[MS_WARPS][32],
@@ -140,7 +168,7 @@ __global__ void __launch_bounds__(MS_THREADS, 5) ms_light_kernel(MsArgs a) {
                 else lo = mid + 1;
             }
             const uint32_t gg = w_g0[warp][lo] + (t - (lo ? w_scan[warp][lo - 1] : 0u));
-            ms_group(a, s_sets, s_live[warp], gg, w_eb[warp][lo], w_ee[warp][lo], w_f[warp][lo]);
+            ms_group(a, s_sets, s_live[warp], ms_load(a, gg), gg, w_eb[warp][lo], w_ee[warp][lo], w_f[warp][lo]);
         }
         __syncwarp();
     }
@@ -158,7 +186,7 @@ __global__ void __launch_bounds__(MS_THREADS) ms_heavy_kernel(MsArgs a) {
         const uint4 item = a.heavy[it];
         const uint32_t eb = __ldg(a.g.row_ptr + item.x), ee = __ldg(a.g.row_ptr + item.x + 1);
         for (uint32_t gg = item.y + threadIdx.x; gg < item.z; gg += MS_THREADS)
-            ms_group(a, s_sets, s_live[warp], gg, eb, ee, item.w);
+            ms_group(a, s_sets, s_live[warp], ms_load(a, gg), gg, eb, ee, item.w);
     }
     ms_flush_live(a, s_live);
 }
@@ -167,7 +195,8 @@ __global__ void __launch_bounds__(MS_THREADS) ms_heavy_kernel(MsArgs a) {
 // them yet, become the next frontier (warp-aggregated appends); vis gains
 // those sets and nxt is cleared.  A thread takes 4 vertices with 16-byte
 // loads (the mask arrays are padded to a multiple of 4 entries).
-__global__ void __launch_bounds__(MS_THREADS) ms_compact_kernel(MsArgs a) {
+__global__ void __launch_bounds__(MS_THREADS) ms_compact_kernel(MsArgs a, bool after_level) {
+    if (after_level && a.mc->nF == 0) return;  // the search has ended: nxt is clear
     const uint32_t lane = threadIdx.x & 31, n4 = (a.g.n + 3) / 4;
     const uint32_t stride = gridDim.x * MS_THREADS;
     uint4* nxt4 = reinterpret_cast<uint4*>(a.nxt);
@@ -204,6 +233,7 @@ __global__ void __launch_bounds__(MS_THREADS) ms_compact_kernel(MsArgs a) {
 
 // Next level: the compacted list becomes the frontier.  <<<1, 1>>>
 __global__ void ms_advance_kernel(MsArgs a) {
+    if (a.mc->nF == 0 && a.mc->nN == 0) return;
     a.mc->nF = a.mc->nN;
     a.mc->nN = 0;
     a.mc->nH = 0;
@@ -326,7 +356,7 @@ static uint32_t ms_grid(const void* kernel, int sms) {
 
 cudaError_t launch_ms_start(const MsArgs& a, int sms, cudaStream_t s) {
     ms_start_kernel<<<1, 32, 0, s>>>(a);
-    ms_compact_kernel<<<(uint32_t)sms * 8, MS_THREADS, 0, s>>>(a);
+    ms_compact_kernel<<<(uint32_t)sms * 8, MS_THREADS, 0, s>>>(a, false);
     ms_advance_kernel<<<1, 1, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -336,7 +366,7 @@ cudaError_t launch_ms_level(const MsArgs& a, int sms, cudaStream_t s) {
     static const uint32_t gh = ms_grid((const void*)ms_heavy_kernel, sms);
     ms_light_kernel<<<gl, MS_THREADS, 0, s>>>(a);
     ms_heavy_kernel<<<gh, MS_THREADS, 0, s>>>(a);
-    ms_compact_kernel<<<(uint32_t)sms * 8, MS_THREADS, 0, s>>>(a);
+    ms_compact_kernel<<<(uint32_t)sms * 8, MS_THREADS, 0, s>>>(a, true);
     ms_advance_kernel<<<1, 1, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -517,6 +517,50 @@ static int ensure_ms_scratch(hbx_pool* p) {
     return HBX_OK;
 }
 
+static MsArgs ms_args(hbx_pool* p) {
+    MsArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = dev_graph(p->g);
+    a.col4 = p->g->col;  // allocated with 16 zero bytes past m entries
+    a.key0 = (uint32_t)p->seed;
+    a.key1 = (uint32_t)(p->seed >> 32);
+    a.epoch = p->o.pool_epoch;
+    a.sets = p->ms_sets;
+    a.vis = p->ms_vis;
+    a.nxt = p->ms_nxt;
+    a.F = p->ms_F;
+    a.Ff = p->ms_N;
+    a.heavy = p->ms_heavy;
+    a.heavy_cap = p->ms_heavy_cap;
+    a.mc = p->ms_c;
+    a.ctr = p->ctr;
+    a.recs = p->recs;
+    a.rowoff = p->ms_rowoff;
+    return a;
+}
+
+// The level loop's CUDA graphs (every argument is a fixed pool buffer; the
+// batch's set ids and count are read from device memory).
+static int ensure_ms_graphs(hbx_pool* p, const MsArgs& a) {
+    if (p->ms_first) return HBX_OK;
+    hbx_ctx* ctx = p->ctx;
+    for (int which = 0; which < 2; which++) {
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = which == 0 ? launch_ms_start(a, ctx->sms, p->stream) : cudaSuccess;
+        for (int l = 0; l < MS_GRAPH_LEVELS && le == cudaSuccess; l++) le = launch_ms_level(a, ctx->sms, p->stream);
+        const cudaError_t ce = cudaStreamEndCapture(p->stream, &graph);
+        if (le != cudaSuccess) return cuda_fail(ctx, le, "level graph capture");
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+        cudaGraphExec_t exec;
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+        (which == 0 ? p->ms_first : p->ms_more) = exec;
+    }
+    return HBX_OK;
+}
+
 // Sample the listed IC sets (ids on the host) MS_SETS at a time with the
 // bit-parallel search.  Dense sets are stored as bitmap rows (MODE_ENCODE) or
 // counted (MODE_HIST); each of the others is encoded (or histogrammed) by one
@@ -531,31 +575,17 @@ static int run_multi_source(hbx_pool* p, uint32_t mode, uint32_t cut, const std:
         const uint32_t nb = (uint32_t)std::min<size_t>(MS_SETS, ids.size() - b0);
         CK(cudaMemcpyAsync(p->ms_sets, ids.data() + b0, (size_t)nb * 4, cudaMemcpyHostToDevice, p->stream));
         CK(cudaMemsetAsync(p->ms_c, 0, sizeof(MsCounters), p->stream));
-        MsArgs a;
-        memset(&a, 0, sizeof(a));
-        a.g = dev_graph(p->g);
-        a.key0 = (uint32_t)p->seed;
-        a.key1 = (uint32_t)(p->seed >> 32);
-        a.epoch = p->o.pool_epoch;
-        a.sets = p->ms_sets;
-        a.nsets = nb;
-        a.vis = p->ms_vis;
-        a.nxt = p->ms_nxt;
-        a.F = p->ms_F;
-        a.Ff = p->ms_N;
-        a.heavy = p->ms_heavy;
-        a.heavy_cap = p->ms_heavy_cap;
-        a.mc = p->ms_c;
-        a.ctr = p->ctr;
-        a.recs = p->recs;
-        a.rowoff = p->ms_rowoff;
+        CK(cudaMemcpyAsync(&p->ms_c->nsets, &nb, 4, cudaMemcpyHostToDevice, p->stream));
+        const MsArgs a = ms_args(p);
+        RC(ensure_ms_graphs(p, a));
         if (timed) CK(cudaEventRecord(p->ev0, p->stream));
-        CK(launch_ms_start(a, ctx->sms, p->stream));
-        p->launches += 3;
-        for (uint64_t level = 0;; level++) {
+        // the levels run from CUDA graphs of MS_GRAPH_LEVELS levels each, the
+        // first one preceded by the roots; the host looks at the frontier
+        // after each graph
+        for (uint64_t level = 0;; level += MS_GRAPH_LEVELS) {
             if (level > (uint64_t)n) return fail(ctx, HBX_ERR_INTERNAL, "bit-parallel search did not end");
-            CK(launch_ms_level(a, ctx->sms, p->stream));
-            p->launches += 4;
+            CK(cudaGraphLaunch(level ? p->ms_more : p->ms_first, p->stream));
+            p->launches += (level ? 0 : 3) + 4 * MS_GRAPH_LEVELS;
             uint32_t nF = 0;
             CK(cudaMemcpyAsync(&nF, &p->ms_c->nF, 4, cudaMemcpyDeviceToHost, p->stream));
             CK(cudaStreamSynchronize(p->stream));
@@ -1247,6 +1277,8 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
     for (void* b : bufs) dfree(c, b);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->ms_first) cudaGraphExecDestroy(p->ms_first);
+    if (p->ms_more) cudaGraphExecDestroy(p->ms_more);
     if (p->evc0) cudaEventDestroy(p->evc0);
     if (p->evc1) cudaEventDestroy(p->evc1);
     if (p->own_stream) cudaStreamDestroy(p->stream);

@@ -104,6 +104,7 @@ struct hbx_pool {
     uint32_t* ms_sets = nullptr;
     unsigned long long* ms_rowoff = nullptr;
     uint32_t* ms_sparse = nullptr;  // mask bits and ids of a batch's sets under the density cut
+    cudaGraphExec_t ms_first = nullptr, ms_more = nullptr;  // the level loop's graphs
     // selection state
     int32_t* cnt = nullptr;
     // counts of sets [0, base_T) before any decrement, kept for the next

@@ -1,0 +1,100 @@
+"""Full-size parity on the twitter7-shaped IC workload (41,652,230 vertices,
+1,468,365,182 edges, p ~ U[0, 0.1)) in the launch configuration the
+benchmark uses (batched form, Huffman + bitmap pool, autotuned shape).
+
+The oracle cannot run a whole IMM at this size (its giant sets scan ~1.4e9
+edges each), so the comparison is on sampled outputs: the first 64 sets of a
+pool (about a fifth of them giant, bitmap-encoded and found by the
+bit-parallel search) set for set, their encodings and edge counts, greedy
+selection on them; and, for a whole IMM, the properties that hold at any size
+(theta from the FP64 bounds, the influence estimate, greedy invariants).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+hbx = pytest.importorskip("paper_2208_00613_gb300")
+
+W_NAME = "ic_rmat42m"
+
+
+@pytest.fixture(scope="module")
+def big():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    hbx.build()
+    w = synth.WORKLOADS[W_NAME]
+    g = w.graph()
+    tc = hbx.torch_context(0)
+    G = hbx.hbx_graph_create(tc.ctx, g)
+    yield w, g, tc, G
+    hbx.hbx_graph_destroy(G)
+    tc.close()
+
+
+def test_fullsize_sets_encodings_selection(big):
+    w, g, tc, G = big
+    T, W, cut = 64, 32, 32
+    p = hbx.hbx_pool_create(tc.ctx, G, "IC", w.rr_seed, hbx.hbx_default_options(encode=1, warmup_sets=W))
+    hbx.hbx_pool_extend(tc.ctx, p, T)
+    op = oracle.Pool(g, oracle.IC, w.rr_seed)
+    op.extend(T, os.cpu_count() or 1)
+    sizes = op.sizes()
+    assert (cut * sizes > g.n).sum() >= 6  # giant sets, found by the bit-parallel search
+    off, verts = hbx.hbx_pool_decode_sets(tc.ctx, p, 0, T)
+    ooff, overts = op.concat(0, T)
+    assert np.array_equal(off, ooff)
+    assert np.array_equal(verts, overts)
+    del verts, overts
+    st = hbx.hbx_pool_stats(tc.ctx, p)
+    sc, lv = op.edge_counts()
+    assert st["edges_scanned"] == sc and st["edges_live"] == lv
+    assert st["sets_bitmap"] == int((cut * sizes > g.n).sum())
+    # encodings against the oracle's encoder with the oracle's codebook
+    f = op.warmup_freq(W, cut)
+    cb_gpu = hbx.hbx_pool_export_codebook(tc.ctx, p, g.n)
+    assert np.array_equal(cb_gpu["freq"], f)
+    cb = oracle.Codebook(g.n, f)
+    assert np.array_equal(cb_gpu["len"], cb.len)
+    assert np.array_equal(cb_gpu["code"], cb.code)
+    giant = [int(j) for j in np.nonzero(cut * sizes > g.n)[0][:3]]
+    for j in list(range(0, T, 8)) + giant:
+        ref = oracle.encode_set(cb, cut, op.set(j))
+        got = hbx.hbx_pool_export_set(tc.ctx, p, j)
+        assert got["kind"] == ref["kind"] and got["size"] == ref["size"], j
+        if ref["kind"] == 0:
+            assert got["bytes"] == ref["bytes"] and np.array_equal(got["raw"], ref["raw"]), j
+        else:
+            assert np.array_equal(got["bitmap"], ref["bitmap"]), j
+    s, m, c = hbx.hbx_pool_select(tc.ctx, p, T, 25)
+    so, mo, co = op.greedy(T, 25)
+    assert s.tolist() == so.tolist() and m.tolist() == mo.tolist() and c == co
+    hbx.hbx_pool_destroy(p)
+
+
+def test_fullsize_imm_invariants(big):
+    w, g, tc, G = big
+    r = hbx.hbx_imm(tc.ctx, G, "IC", w.k, w.eps, w.ell, w.rr_seed)
+    st, seeds, marg = r["stats"], r["seeds"], r["marginal"]
+    n = g.n
+    # theta from the FP64 bounds of the IMM reading of Eq. (1), as the oracle states them
+    b = oracle.imm_params(n, w.k, w.eps, w.ell)
+    T_last = 0
+    for i in range(1, st["rounds"] + 1):
+        T_last = max(T_last, math.ceil(b["lambda_p"] / (n / 2.0 ** i)))
+    assert st["theta"] == max(T_last, math.ceil(b["lambda_star"] / st["lb"]))
+    # the estimate, the greedy invariants, and the pool's make-up
+    assert r["influence"] == n * st["covered"] / st["theta"]
+    assert len(set(seeds.tolist())) == w.k
+    assert int(marg.sum()) == st["covered"]
+    assert all(marg[i] >= marg[i + 1] for i in range(w.k - 1))
+    assert st["sets_bitmap"] > 0 and st["sets_huffman"] > 0
+    assert st["raw_int32_bytes"] >= 4 * st["pool_bytes"]  # at least 4x below the int32 pool
