@@ -102,17 +102,27 @@ def graph_bytes(g):
 
 def oracle_sample_rate(g, w, target_s=15.0, budget_sets=None):
     """Oracle throughput on a bounded sample: sample S sets of the workload on
-    all host cores, then greedy k on them; returns (sets/s, S, cores, seconds)."""
+    all host cores, then greedy k on them; returns (sets/s, S, cores, seconds).
+    S is sized from a probe (doubling from 16 sets until a probe takes a
+    second) so that the measured leg takes about target_s."""
     import oracle
     model = oracle.IC if w.model == "IC" else oracle.LT
     cores = os.cpu_count() or 1
-    probe = oracle.Pool(g, model, w.rr_seed)
-    t0 = time.perf_counter()
-    probe.extend(2000, cores)
-    probe.greedy(2000, w.k)
-    dt = time.perf_counter() - t0
-    S = budget_sets or max(2000, int(2000 * target_s / max(dt, 1e-3)))
-    S = min(S, 2_000_000)
+    S = budget_sets
+    if S is None:
+        probe_n = 16
+        while True:
+            probe = oracle.Pool(g, model, w.rr_seed)
+            t0 = time.perf_counter()
+            probe.extend(probe_n, cores)
+            probe.greedy(probe_n, w.k)
+            dt = time.perf_counter() - t0
+            del probe
+            if dt >= 1.0 or probe_n >= 2048:
+                break
+            probe_n *= 2
+        S = max(16, int(probe_n * target_s / max(dt, 1e-3)))
+        S = min(S, 2_000_000)
     pool = oracle.Pool(g, model, w.rr_seed)
     t0 = time.perf_counter()
     pool.extend(S, cores)

@@ -167,6 +167,9 @@ WORKLOADS = {
     "wc_rmat1m": Workload("wc_rmat1m", 1 << 20, 1 << 24, 2, "IC", "wc", 50, 0.5, 1.0, 7, 1),
     # LT on a LiveJournal-sized graph
     "lt_rmat4m": Workload("lt_rmat4m", 1 << 22, 1 << 26, 3, "LT", "lt", 100, 0.3, 1.0, 7, 1),
+    # the same kind of graph at 2^23 vertices, 2^28 edges: a profiling-size case
+    # of the full-size kernels (a few GB on the device)
+    "ic_rmat8m": Workload("ic_rmat8m", 1 << 23, 1 << 28, 78, "IC", "uniform0.1", 100, 0.5, 1.0, 7, 1),
     # IC on a twitter7-sized graph (41.65M vertices, 1.468B edges)
     "ic_rmat42m": Workload("ic_rmat42m", 41652230, 1468365182, 4, "IC", "uniform0.1", 100, 0.5, 1.0, 7, 1),
 }
