@@ -33,9 +33,9 @@ constexpr int MS_THREADS = 256;
 constexpr int MS_WARPS = MS_THREADS / 32;
 // A warp takes 32 frontier vertices of at most MS_HEAVY edge groups each, so
 // no warp holds more than 1024 groups; bigger vertices are cut into chunks of
-// MS_CHUNK groups that whole blocks take.
+// MS_CHUNK groups, one warp per chunk.
 constexpr uint32_t MS_HEAVY = 32;
-constexpr uint32_t MS_CHUNK = 1024;
+constexpr uint32_t MS_CHUNK = 256;
 
 // Per-warp live-edge counts of the batch's sets in shared memory, added to the
 // batch totals when the warp is done.
@@ -179,13 +179,13 @@ __global__ void __launch_bounds__(MS_THREADS) ms_heavy_kernel(MsArgs a) {
     __shared__ uint32_t s_sets[MS_SETS];
     __shared__ uint32_t s_live[MS_WARPS][MS_SETS];
     const uint32_t nH = min(a.mc->nH, a.heavy_cap);
-    if (blockIdx.x >= nH) return;
+    if (blockIdx.x * MS_WARPS >= nH) return;
     ms_init_shared(a, s_sets, s_live);
-    const uint32_t warp = threadIdx.x >> 5;
-    for (uint32_t it = blockIdx.x; it < nH; it += gridDim.x) {
-        const uint4 item = a.heavy[it];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (uint32_t it = blockIdx.x * MS_WARPS + warp; it < nH; it += gridDim.x * MS_WARPS) {
+        const uint4 item = a.heavy[it];  // one chunk per warp
         const uint32_t eb = __ldg(a.g.row_ptr + item.x), ee = __ldg(a.g.row_ptr + item.x + 1);
-        for (uint32_t gg = item.y + threadIdx.x; gg < item.z; gg += MS_THREADS)
+        for (uint32_t gg = item.y + lane; gg < item.z; gg += 32)
             ms_group(a, s_sets, s_live[warp], ms_load(a, gg), gg, eb, ee, item.w);
     }
     ms_flush_live(a, s_live);

@@ -506,9 +506,9 @@ static int ensure_ms_scratch(hbx_pool* p) {
     RC(grow_buffer(p, (void**)&p->ms_F, 0, n4, 0));
     RC(grow_buffer(p, (void**)&p->ms_N, 0, n4, 0));
     // a heavy vertex has more than 32 edge groups, so at most m/128 of them,
-    // each cut into chunks of 1024 groups
+    // each cut into chunks of 256 groups
     const uint64_t m = p->g->m;
-    p->ms_heavy_cap = (uint32_t)std::min<uint64_t>(m / 128 + m / 4096 + 1024, 0xFFFFFFFFull);
+    p->ms_heavy_cap = (uint32_t)std::min<uint64_t>(m / 128 + m / 1024 + 1024, 0xFFFFFFFFull);
     RC(grow_buffer(p, (void**)&p->ms_heavy, 0, (size_t)p->ms_heavy_cap * sizeof(uint4), 0));
     RC(grow_buffer(p, (void**)&p->ms_c, 0, sizeof(MsCounters), 0));
     RC(grow_buffer(p, (void**)&p->ms_sets, 0, MS_SETS * 4, 0));
