@@ -314,8 +314,9 @@ def run_hbx(args, rank, world, local_rank):
     # launched round by round) on the same workload and seed, same timing rules
     plain = None
     if not args.no_plain and args.form == 1:
-        popts = hbx.hbx_default_options(encode=0, form=0)
-        hbx.hbx_imm(ctx, G, w.model, w.k, w.eps, w.ell, seed, popts)  # warm-up
+        popts = hbx.hbx_default_options(encode=args.plain_encode, form=0)
+        for _ in range(args.plain_warmup):
+            hbx.hbx_imm(ctx, G, w.model, w.k, w.eps, w.ell, seed, popts)
         pms, pr = [], None
         for _ in range(args.steps):
             with torch.cuda.stream(tc.stream):
@@ -328,7 +329,8 @@ def run_hbx(args, rank, world, local_rank):
             pms.append(ev0.elapsed_time(ev1))
         pmean = sum(pms) / len(pms)
         plain = {"ms_per_step": pmean, "value": pr["stats"]["theta"] / (pmean / 1000.0), "unit": UNIT,
-                 "encode": "int32", "batched_speedup": pmean / (total_ms / args.steps),
+                 "encode": "huffman+bitmap" if args.plain_encode else "int32",
+                 "batched_speedup": pmean / (total_ms / args.steps), "warmup": args.plain_warmup,
                  "seeds_equal": bool(np.array_equal(pr["seeds"], r["seeds"])),
                  "influence_equal": pr["influence"] == r["influence"]}
     serving = None
@@ -419,6 +421,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison leg")
     ap.add_argument("--serving", type=int, default=0, help="queries of the serving leg (0: skip)")
+    ap.add_argument("--plain-warmup", type=int, default=1, help="untimed plain-form IMMs before its timed ones")
+    ap.add_argument("--plain-encode", type=int, default=0,
+                    help="encoding of the plain-form leg (1 where an int32 pool would not fit the GPU)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
