@@ -314,6 +314,9 @@ def run_hbx(args, rank, world, local_rank):
     # launched round by round) on the same workload and seed, same timing rules
     plain = None
     if not args.no_plain and args.form == 1:
+        # return the batched pools' memory, cached by torch's allocator, to the
+        # device: the plain form grows its heaps by copying (old + new at once)
+        torch.cuda.empty_cache()
         popts = hbx.hbx_default_options(encode=args.plain_encode, form=0)
         for _ in range(args.plain_warmup):
             hbx.hbx_imm(ctx, G, w.model, w.k, w.eps, w.ell, seed, popts)
