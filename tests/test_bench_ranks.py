@@ -58,3 +58,23 @@ def test_reference_arm_other_ranks_do_nothing(capsys):
         gpus = 2
     bench.run_reference(A(), rank=1)
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_sample_is_bounded_and_positive():
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    w = synth.WORKLOADS["ic_rmat4k"]
+    rate, S, cores, dt = bench.oracle_sample_rate(w.graph(), w, target_s=0.5)
+    assert rate > 0 and S >= 16 and cores >= 1
+    assert dt < 30.0  # the probe sizes the sample to about target_s
+
+
+def test_count_roofline_from_stats():
+    sys.path.insert(0, ROOT)
+    import bench
+    stats = [{"count_kernel_s": 0.01, "count_bytes": 30_000_000_000}, {"count_kernel_s": 0.01,
+                                                                      "count_bytes": 30_000_000_000}]
+    r = bench.count_roofline(stats, 6000.0)
+    assert abs(r["achieved"] - 3000.0) < 1e-9 and abs(r["frac"] - 0.5) < 1e-12
+    assert bench.count_roofline([{"count_kernel_s": 0.0, "count_bytes": 0}], 6000.0) is None
