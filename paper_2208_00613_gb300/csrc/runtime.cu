@@ -921,12 +921,6 @@ static int choose_shape(hbx_pool* p, Shape* out) {
     return HBX_OK;
 }
 
-int pool_set_warmup(hbx_pool* p, uint64_t W) {
-    if (p->has_cb) return HBX_OK;
-    p->W = W;
-    return HBX_OK;
-}
-
 static int ensure_codebook(hbx_pool* p) {
     hbx_ctx* ctx = p->ctx;
     if (!p->o.encode || p->has_cb) return HBX_OK;

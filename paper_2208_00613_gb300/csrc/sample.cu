@@ -13,25 +13,35 @@
 //          point weights exceeds x, and stops when there is none or that source
 //          is already in the set.
 //
-// Two kernels:
-//   sample_warp_kernel   one warp per set.  The set's vertex list (the BFS queue)
-//                        and a hash set of visited ids live in shared memory.  A
-//                        set that outgrows the warp's capacity QW, or whose
-//                        frontier would exceed the warp's edge-group budget, is
-//                        handed to the block kernel.  The finished set is encoded
-//                        by the same warp: a bitmap if cut*|R| > n, else its
-//                        vertices are mapped to codebook ranks, sorted (bitonic),
-//                        and the codes bit-packed over a prefix sum of lengths.
+// Kernels:
+//   sample_warp_kernel   one warp per set, persistent over the batch (work
+//                        stealing).  The set's vertex list (the BFS queue) and a
+//                        hash set of visited ids live in shared memory.  A set
+//                        that outgrows the warp's capacity QW, or whose frontier
+//                        would exceed the warp's edge-group budget, is handed on.
+//                        The finished set is encoded by the same warp: a bitmap if
+//                        cut*|R| > n, else its vertices are mapped to codebook
+//                        ranks, sorted (bitonic), and the codes bit-packed over a
+//                        prefix sum of lengths.
+//   sample_mid_kernel    one 512-thread block per set handed on by a warp, up to
+//                        4096 vertices, everything in shared memory; a single warp
+//                        runs ahead while the frontier is thin.  IC sets that
+//                        outgrow it go to the bit-parallel search (msbfs.cu) in
+//                        encoded pools and histogram passes, the others to the
+//                        block kernel.
 //   sample_block_kernel  one thread-block cluster (1 to 8 blocks of 512 threads)
-//                        per heavy set: level-synchronous BFS whose edge groups
-//                        are spread over all blocks of the cluster (a block-wide
-//                        scan of group counts per 512 frontier vertices), level
-//                        barriers on the cluster barrier, the queue tail in block
-//                        0's shared memory (reached by the others through
-//                        distributed shared memory), the visited set as an n-bit
-//                        bitmap and the queue in HBM.  The visited bitmap is the
-//                        bitmap encoding; small Huffman sets are sorted in shared
-//                        memory, large ones through a rank bitmap.
+//                        per set: level-synchronous BFS whose edge groups are
+//                        spread over all blocks of the cluster (a block-wide scan
+//                        of group counts per 512 frontier vertices), level barriers
+//                        on the cluster barrier, the queue tail in block 0's shared
+//                        memory (reached by the others through distributed shared
+//                        memory), the visited set as an n-bit bitmap and the queue
+//                        in HBM.  The visited bitmap is the bitmap encoding; small
+//                        Huffman sets are sorted in shared memory, large ones
+//                        through a rank bitmap.  The plain form samples every set
+//                        with this kernel.
+//   sample_ms_sparse_kernel  encodes a bit-parallel search's sets that fall under
+//                        the density cut, one block each, as the block kernel does.
 #include <cstdio>
 
 #include <cooperative_groups.h>
