@@ -59,7 +59,8 @@ struct DevGraph {
     uint32_t m;
     const uint32_t* row_ptr;  // n+1
     const uint32_t* col;      // m
-    const float* prob;        // IC: 4*ceil(m/4) floats, 16-byte aligned, zero padded
+    const uint32_t* thr;      // IC: live threshold ceil(p * 2^24) per edge, 4*ceil(m/4) entries,
+                              // 16-byte aligned, zero padded
     const uint32_t* q;        // LT: floor(w * 2^32), capped at 2^32-1
 };
 
@@ -149,7 +150,9 @@ __device__ __forceinline__ void set_error(Counters* c, unsigned long long code) 
 
 // IC coin of Section 2.1: edge e is live in sample j when the top 24 bits of
 // its Philox word, as a fraction of 2^24 (exact in fp32), fall below p(e).
-__device__ __forceinline__ bool ic_live(uint32_t x, float p) { return (float)(x >> 8) * 0x1p-24f < p; }
+// With a = x >> 8 an integer and p * 2^24 exact, a * 2^-24 < p holds exactly
+// when a < ceil(p * 2^24), the threshold stored per edge at graph upload.
+__device__ __forceinline__ bool ic_live(uint32_t x, uint32_t thr) { return (x >> 8) < thr; }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;

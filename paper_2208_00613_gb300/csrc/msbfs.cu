@@ -55,13 +55,13 @@ __device__ __forceinline__ void ms_flush_live(const MsArgs& a, uint32_t (*s_live
 
 // The probabilities and sources of one aligned group of 4 in-edges.
 struct MsGroupData {
-    float4 p;
-    uint4 c;
+    uint4 p;  // live thresholds
+    uint4 c;  // sources
 };
 
 __device__ __forceinline__ MsGroupData ms_load(const MsArgs& a, uint32_t gg) {
     MsGroupData d;
-    d.p = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
+    d.p = __ldg(reinterpret_cast<const uint4*>(a.g.thr) + gg);
     d.c = __ldg(reinterpret_cast<const uint4*>(a.col4) + gg);
     return d;
 }

@@ -258,7 +258,13 @@ extern "C" int hbx_graph_create(hbx_ctx* ctx, uint32_t n, uint64_t m, const uint
     int r = up((void**)&g->row_ptr, row_ptr, ((size_t)n + 1) * 4, ((size_t)n + 1) * 4);
     if (!r) r = up((void**)&g->col, col, m * 4, m * 4 + 16);
     const size_t m4 = ((m + 3) / 4) * 4;
-    if (!r && ic_prob) r = up((void**)&g->prob, ic_prob, m * 4, m4 * 4 + 16);
+    if (!r && ic_prob) {
+        // the IC coin a * 2^-24 < p (a = top 24 bits of a Philox word) as the
+        // integer compare a < ceil(p * 2^24); p * 2^24 is exact in double
+        std::vector<uint32_t> thr(m);
+        for (uint64_t e = 0; e < m; e++) thr[e] = (uint32_t)std::ceil((double)ic_prob[e] * 16777216.0);
+        r = up((void**)&g->thr, thr.data(), m * 4, m4 * 4 + 16);
+    }
     if (!r && lt_weight) r = up((void**)&g->q, q.data(), m * 4, m * 4 + 16);
     if (!r) {
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -267,7 +273,7 @@ extern "C" int hbx_graph_create(hbx_ctx* ctx, uint32_t n, uint64_t m, const uint
     if (r) {
         dfree(ctx, g->row_ptr);
         dfree(ctx, g->col);
-        dfree(ctx, g->prob);
+        dfree(ctx, g->thr);
         dfree(ctx, g->q);
         delete g;
         return r;
@@ -286,7 +292,7 @@ extern "C" void hbx_graph_destroy(hbx_graph* g) {
         if (p->g == g) hbx_pool_destroy(p);
     dfree(c, g->row_ptr);
     dfree(c, g->col);
-    dfree(c, g->prob);
+    dfree(c, g->thr);
     dfree(c, g->q);
     c->graphs.erase(g);
     delete g;
@@ -303,7 +309,7 @@ static DevGraph dev_graph(const hbx_graph* g) {
     d.m = g->m;
     d.row_ptr = g->row_ptr;
     d.col = g->col;
-    d.prob = g->prob;
+    d.thr = g->thr;
     d.q = g->q;
     return d;
 }
@@ -1218,7 +1224,7 @@ extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint
     if (!ctx || !g || !out) return HBX_ERR_INVALID_ARG;
     *out = nullptr;
     if (model != HBX_IC && model != HBX_LT) return fail(ctx, HBX_ERR_INVALID_ARG, "unknown model");
-    if (model == HBX_IC && !g->prob) return fail(ctx, HBX_ERR_INVALID_ARG, "graph has no IC probabilities");
+    if (model == HBX_IC && !g->thr) return fail(ctx, HBX_ERR_INVALID_ARG, "graph has no IC probabilities");
     if (model == HBX_LT && !g->q) return fail(ctx, HBX_ERR_INVALID_ARG, "graph has no LT weights");
     hbx_options o;
     hbx_default_options(&o);

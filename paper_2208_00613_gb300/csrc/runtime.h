@@ -55,7 +55,7 @@ struct hbx_graph {
     uint64_t fingerprint = 0;  // hash of sizes and sampled CSR entries
     uint32_t* row_ptr = nullptr;
     uint32_t* col = nullptr;
-    float* prob = nullptr;  // 4*ceil(m/4) floats
+    uint32_t* thr = nullptr;  // IC live thresholds ceil(p * 2^24), 4*ceil(m/4) entries
     uint32_t* q = nullptr;  // LT fixed-point weights
 };
 

@@ -5,9 +5,10 @@
 // vertex id, set id j, epoch, stream), so the set does not depend on the order
 // in which the search meets its edges:
 //   root   = floor(x * n / 2^32),  x = word 0 of Philox(0, j, epoch, 3)
-//   IC     in-edge e is live iff (x >> 8) * 2^-24 < p[e] (exact fp32), x = word
-//          e%4 of Philox(e/4, j, epoch, 1): one draw serves the 4 edges of an
-//          aligned group, and a thread handles one group (one float4 of p)
+//   IC     in-edge e is live iff (x >> 8) * 2^-24 < p[e] (exact fp32), i.e.
+//          (x >> 8) < ceil(p[e] * 2^24), x = word e%4 of Philox(e/4, j, epoch,
+//          1): one draw serves the 4 edges of an aligned group, and a thread
+//          handles one group (one uint4 of thresholds)
 //   LT     at vertex v, x = word 0 of Philox(v, j, epoch, 2); the walk moves to
 //          the source of the first in-edge whose inclusive prefix sum of fixed-
 //          point weights exceeds x, and stops when there is none or that source
@@ -89,14 +90,14 @@ __device__ __forceinline__ bool hash_insert(uint32_t* h, uint32_t mask, uint32_t
 // Returns the live mask; adds the in-range edge count to *scanned.
 __device__ __forceinline__ uint32_t group_coins(const SampleArgs& a, uint32_t j, uint32_t gg, uint32_t eb,
                                                 uint32_t ee, unsigned long long* scanned) {
-    const float4 p4 = __ldg(reinterpret_cast<const float4*>(a.g.prob) + gg);
+    const uint4 t4 = __ldg(reinterpret_cast<const uint4*>(a.g.thr) + gg);
     const uint4 x = philox4x32_10(make_uint4(gg, j, a.epoch, STREAM_IC), a.key0, a.key1);
     const uint32_t e0 = gg * 4u;
     const bool v0 = e0 >= eb && e0 < ee, v1 = e0 + 1 >= eb && e0 + 1 < ee;
     const bool v2 = e0 + 2 >= eb && e0 + 2 < ee, v3 = e0 + 3 >= eb && e0 + 3 < ee;
     *scanned += (uint32_t)v0 + (uint32_t)v1 + (uint32_t)v2 + (uint32_t)v3;
-    return (uint32_t)(v0 && ic_live(x.x, p4.x)) | ((uint32_t)(v1 && ic_live(x.y, p4.y)) << 1) |
-           ((uint32_t)(v2 && ic_live(x.z, p4.z)) << 2) | ((uint32_t)(v3 && ic_live(x.w, p4.w)) << 3);
+    return (uint32_t)(v0 && ic_live(x.x, t4.x)) | ((uint32_t)(v1 && ic_live(x.y, t4.y)) << 1) |
+           ((uint32_t)(v2 && ic_live(x.z, t4.z)) << 2) | ((uint32_t)(v3 && ic_live(x.w, t4.w)) << 3);
 }
 
 // Bitonic sort of 32 keys held one per lane (ascending by lane).

@@ -269,7 +269,7 @@ extern "C" int hbx_submit(hbx_server* s, hbx_graph* g, hbx_model model, uint32_t
     if (q->o.density_cut == 0) q->o.density_cut = 32;
     double lp, ls;
     if (!imm_lambda(g->n, k, eps, ell, &lp, &ls)) return fail(s->ctx, HBX_ERR_INVALID_ARG, "bad k, eps, ell or n");
-    if ((model == HBX_IC && !g->prob) || (model == HBX_LT && !g->q) || (model != HBX_IC && model != HBX_LT))
+    if ((model == HBX_IC && !g->thr) || (model == HBX_LT && !g->q) || (model != HBX_IC && model != HBX_LT))
         return fail(s->ctx, HBX_ERR_INVALID_ARG, "graph lacks the model's parameters");
     if (q->o.encode && q->o.warmup_sets == 0) {
         // fix the warm-up block of a served pool independently of the query:
