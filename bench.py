@@ -230,7 +230,7 @@ def run_reference(args, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "m": w.m, "model": w.model, "weights": w.weights, "k": w.k,
+        "config": {"workload": w.name, "n": w.n, "m": w.m, "diffusion": w.model, "weights": w.weights, "k": w.k,
                    "eps": w.eps, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -366,7 +366,7 @@ def run_hbx(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "m": w.m, "model": w.model, "weights": w.weights, "k": w.k,
+        "config": {"workload": w.name, "n": w.n, "m": w.m, "diffusion": w.model, "weights": w.weights, "k": w.k,
                    "eps": w.eps, "ell": w.ell, "encode": "huffman+bitmap" if args.encode else "int32",
                    "form": "persistent+graph" if args.form else "plain", "parallelism": f"replicas{world}",
                    "l2": "flushed (512 MB write) between timed steps"},
