@@ -76,3 +76,56 @@ def test_product_never_reaches_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f
                 assert "liboracle" not in txt and "oracle.cpp" not in txt, f
+
+
+def _arities():
+    """Parameter count of every function include/hbx.h declares."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(hbx_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        p = params.strip()
+        # commas inside function-pointer parameters belong to those parameters
+        depth, count = 0, 0 if p in ("", "void") else 1
+        for ch in p:
+            depth += ch == "("
+            depth -= ch == ")"
+            count += ch == "," and depth == 0
+        out[name] = count
+    return out
+
+
+def test_binding_argtypes_match_header(lib):
+    ar = _arities()
+    assert len(ar) >= 20
+    for name, n in ar.items():
+        f = getattr(lib, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+
+
+def test_struct_layout_matches_header(lib, tmp_path):
+    """The binding's ctypes structs against the C compiler's layout of the
+    header's structs: sizes and every field offset."""
+    import ctypes
+    import paper_2208_00613_gb300 as hbx
+    fields = {"hbx_options": [f for f, _ in hbx.hbx_options._fields_],
+              "hbx_stats": [f for f, _ in hbx.hbx_stats._fields_]}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hbx.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        st, key, val = line.split()
+        got[(st, key)] = int(val)
+    for st, cls in (("hbx_options", hbx.hbx_options), ("hbx_stats", hbx.hbx_stats)):
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
