@@ -403,10 +403,12 @@ def ctypes_sizeof_stats(hbx):
 
 
 def source_hash():
+    """Hash of the sampler kernels' sources (their device code and launchers):
+    a stored DRAM-traffic capture is used only while these are unchanged."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2208_00613_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in ("common.cuh", "internal.h", "sample.cu", "msbfs.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -12,6 +12,7 @@
 #include <mutex>
 #include <set>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -200,12 +201,40 @@ extern "C" int hbx_graph_create(hbx_ctx* ctx, uint32_t n, uint64_t m, const uint
         if (row_ptr[v + 1] < row_ptr[v]) return fail(ctx, HBX_ERR_INVALID_ARG, "row_ptr decreases");
         max_deg = std::max(max_deg, row_ptr[v + 1] - row_ptr[v]);
     }
-    for (uint64_t e = 0; e < m; e++)
-        if (col[e] >= n) return fail(ctx, HBX_ERR_INVALID_ARG, "col id out of range");
-    if (ic_prob)
-        for (uint64_t e = 0; e < m; e++)
-            if (!(ic_prob[e] >= 0.0f && ic_prob[e] <= 1.0f))
-                return fail(ctx, HBX_ERR_INVALID_ARG, "IC probability outside [0,1]");
+    // Edge checks and the IC live thresholds, over the host's cores.  The IC coin
+    // a * 2^-24 < p (a = top 24 bits of a Philox word) is the integer compare
+    // a < ceil(p * 2^24); p * 2^24 is exact in double.
+    std::vector<uint32_t> thr(ic_prob ? m : 0);
+    {
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const unsigned T = m < (1u << 20) ? 1u : std::min(hw, 32u);
+        std::vector<int> bad(T, 0);  // 1: col out of range, 2: probability outside [0,1]
+        auto check = [&](unsigned t) {
+            const uint64_t e0 = m * t / T, e1 = m * (t + 1) / T;
+            for (uint64_t e = e0; e < e1; e++) {
+                if (col[e] >= n) {
+                    bad[t] = 1;
+                    return;
+                }
+                if (ic_prob) {
+                    const float p = ic_prob[e];
+                    if (!(p >= 0.0f && p <= 1.0f)) {
+                        bad[t] = 2;
+                        return;
+                    }
+                    thr[e] = (uint32_t)std::ceil((double)p * 16777216.0);
+                }
+            }
+        };
+        std::vector<std::thread> pool;
+        for (unsigned t = 1; t < T; t++) pool.emplace_back(check, t);
+        check(0);
+        for (auto& th : pool) th.join();
+        for (unsigned t = 0; t < T; t++) {
+            if (bad[t] == 1) return fail(ctx, HBX_ERR_INVALID_ARG, "col id out of range");
+            if (bad[t] == 2) return fail(ctx, HBX_ERR_INVALID_ARG, "IC probability outside [0,1]");
+        }
+    }
     std::vector<uint32_t> q;
     if (lt_weight) {
         q.resize(m ? m : 1);
@@ -258,13 +287,7 @@ extern "C" int hbx_graph_create(hbx_ctx* ctx, uint32_t n, uint64_t m, const uint
     int r = up((void**)&g->row_ptr, row_ptr, ((size_t)n + 1) * 4, ((size_t)n + 1) * 4);
     if (!r) r = up((void**)&g->col, col, m * 4, m * 4 + 16);
     const size_t m4 = ((m + 3) / 4) * 4;
-    if (!r && ic_prob) {
-        // the IC coin a * 2^-24 < p (a = top 24 bits of a Philox word) as the
-        // integer compare a < ceil(p * 2^24); p * 2^24 is exact in double
-        std::vector<uint32_t> thr(m);
-        for (uint64_t e = 0; e < m; e++) thr[e] = (uint32_t)std::ceil((double)ic_prob[e] * 16777216.0);
-        r = up((void**)&g->thr, thr.data(), m * 4, m4 * 4 + 16);
-    }
+    if (!r && ic_prob) r = up((void**)&g->thr, thr.data(), m * 4, m4 * 4 + 16);
     if (!r && lt_weight) r = up((void**)&g->q, q.data(), m * 4, m * 4 + 16);
     if (!r) {
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
