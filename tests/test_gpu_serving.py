@@ -3,14 +3,17 @@
 Every query's result in the mix (queries arriving while others run, pools
 shared and extended across queries, several pools in flight on their own
 streams) must equal the same query run alone through hbx_imm: seeds and the
-FP64 influence estimate, exactly.  Also: cancellation of a queued query, a
-bounded wait that runs out, and admission rejection by projected footprint.
+FP64 influence estimate, exactly.  Each alone result in turn must equal the
+oracle's IMM on the same graph, model and seed.  Also: cancellation of a
+queued query, a bounded wait that runs out, and admission rejection by
+projected footprint.
 """
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -43,9 +46,16 @@ def test_mix_equals_alone(env):
     qs = synth.poisson_queries(seed=3, count=16, rate_per_s=200.0, graphs=[0, 1, 2], k_range=(5, 40),
                                eps_choices=(0.3, 0.5))
     alone = []
+    pools = {}  # oracle pools per (graph, model); IMM reuses a pool's sets as a prefix
     for q in qs:
         r = hbx.hbx_imm(tc.ctx, handles[q["graph"]], q["model"], q["k"], q["eps"], 1.0, 7)
         alone.append(r)
+        key = (q["graph"], q["model"])
+        if key not in pools:
+            pools[key] = oracle.Pool(gs[q["graph"]], oracle.IC if q["model"] == "IC" else oracle.LT, 7)
+        o = pools[key].imm(q["k"], q["eps"], 1.0)
+        assert np.array_equal(r["seeds"], o["seeds"]), q
+        assert r["influence"] == o["influence"] and r["stats"]["theta"] == o["theta"], q
     srv = hbx.hbx_server_create(tc.ctx, 3, 0)
     try:
         tickets = []

@@ -73,6 +73,24 @@ def test_huffman_single_symbol_and_length_limit():
     assert np.all(np.diff(lens[order].astype(np.int64)) <= 0)
 
 
+def test_huffman_tie_rules_and_rescale_worked_cases():
+    """Cases worked by hand under the codebook reading (Section 4.2.2): the
+    leaf-first tie rule, the (f, id) symbol order and the ceil(f/2) rescale
+    each decide one of them, so changing any of the three fails here."""
+    rows = read_golden("huffman_ties.txt")
+    assert len(rows) == 6
+    for fr, lr in zip(rows[0::2], rows[1::2]):
+        f = [int(x) for x in fr.split()[1:]]
+        want = [int(x) for x in lr.split()[1:]]
+        assert oracle.huffman_lengths(f).tolist() == want, f[:4]
+    # the Fibonacci weights need the rescale: the partial sums stay below the
+    # next-but-one leaf (F1 + ... + Fi = F(i+2) - 1), so the first build is a
+    # chain in which v0 and v1 sit 33 deep
+    fib = [int(x) for x in rows[4].split()[1:]]
+    assert all(sum(fib[:i + 1]) == fib[i + 2] - 1 for i in range(32))
+    assert abs(_kraft([int(x) for x in rows[5].split()[1:]]) - 1.0) < 1e-12
+
+
 def test_canonical_rfc1951():
     d = {r.split()[0]: r.split()[1:] for r in read_golden("rfc1951_canonical.txt")}
     lengths = [int(x) for x in d["lengths"]]
