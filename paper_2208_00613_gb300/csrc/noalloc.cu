@@ -14,6 +14,12 @@
 // contents behind; the finish counter is cleared before each launch.  Calls
 // whose launches overlap on the GPU (for example on two streams at once) race
 // on the shared array, so a caller must order them (one stream, or events).
+//
+// CUDA loads a module's device code lazily, on first use, and that load itself
+// reserves device memory.  The first call on each device therefore loads this
+// kernel explicitly and looks up the array's address; a caller makes that call
+// (or the set-up-only call with null pointers and n = 0) before reserving its
+// memory budget, and every later call allocates nothing.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -99,6 +105,13 @@ static int scratch_for_current_device(NoAllocScratch** out) {
     }
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_ready[dev]) {
+        // load the module on this device now (lazy loading would do it at the
+        // first launch), then resolve the array's device address
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, argmax_noalloc_kernel) != cudaSuccess) {
+            cudaGetLastError();
+            return HBX_ERR_CUDA;
+        }
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_argmax_scratch);
         if (e != cudaSuccess || p == nullptr) {
@@ -116,11 +129,16 @@ static int scratch_for_current_device(NoAllocScratch** out) {
 
 extern "C" int hbx_argmax_noalloc(const int32_t* d_counts, uint32_t n, uint32_t* d_out, void* cuda_stream) {
     using namespace hbx;
-    if (!d_counts || !d_out || n == 0 || (uint64_t)n > HBX_ARGMAX_NOALLOC_MAX) return HBX_ERR_INVALID_ARG;
+    const bool setup_only = !d_counts && !d_out && n == 0;
+    if (!setup_only && (!d_counts || !d_out || n == 0 || (uint64_t)n > HBX_ARGMAX_NOALLOC_MAX))
+        return HBX_ERR_INVALID_ARG;
     NoAllocScratch* scr = nullptr;
     const int r = scratch_for_current_device(&scr);
-    if (r != HBX_OK) return r;
+    if (r != HBX_OK || setup_only) return r;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // The last block of every finished launch sets the counter back to 0; this
+    // clear guards against a launch that never finished (an aborted context or
+    // a launch error), which would leave it non-zero.
     if (cudaMemsetAsync(&scr->ticket, 0, sizeof(unsigned int), s) != cudaSuccess) {
         cudaGetLastError();
         return HBX_ERR_CUDA;
