@@ -72,6 +72,11 @@ def _load():
         "orc_canonical": (U32, [U64, P, P, P]),
         "orc_encode_set": (I, [U32, U32, P, P, P, P, U64, P, P, P, P, U64, P, P, P, U64]),
         "orc_decode_set": (ctypes.c_int64, [U32, P, P, U32, U32, U64, P, P, U32, P, P]),
+        "orc_pool_greedy_recount": (I, [P, U64, U32, P, P, P]),
+        "orc_pool_scheme": (I, [P, U64, P]),
+        "orc_pool_bitmax_tiles": (I, [P, U64, P]),
+        "orc_bitmax_query": (I, [U32, U64, P, U32, P, P, P]),
+        "orc_huffmax_query": (I, [U32, P, P, U64, P, P, P, P, P, P, P, P, P, P, U32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -202,11 +207,81 @@ class Pool:
                     covered=cov.value, lb=lb.value, rounds=rounds.value,
                     round_T=rT[:rounds.value + 1].copy())
 
+    def greedy_recount(self, T: int, k: int):
+        """Greedy with the table rebuilt every iteration (Algorithms 2 and 3)."""
+        seeds = np.empty(k, dtype=np.uint32)
+        marg = np.empty(k, dtype=np.uint64)
+        cov = ctypes.c_uint64()
+        if _load().orc_pool_greedy_recount(self.h, T, k, _p(seeds), _p(marg), ctypes.byref(cov)) != 0:
+            raise ValueError("orc_pool_greedy_recount: bad arguments")
+        return seeds, marg, cov.value
+
+    def scheme(self, W: int):
+        """(True for Bitmax / False for Huffmax, skewness of the warm-up sizes):
+        Algorithm 1's Characterize over sets [0, W)."""
+        sk = ctypes.c_double()
+        r = _load().orc_pool_scheme(self.h, W, ctypes.byref(sk))
+        if r < 0:
+            raise ValueError("warm-up block larger than the pool")
+        return bool(r), sk.value
+
+    def bitmax_tiles(self, T: int) -> np.ndarray:
+        """Vertex-major Bitmax tiles of sets [0, T): shape (ceil(T/32), n)."""
+        nt = (T + 31) // 32
+        out = np.empty(max(nt * self.n, 1), dtype=np.uint32)
+        if _load().orc_pool_bitmax_tiles(self.h, T, _p(out)) != 0:
+            raise ValueError("orc_pool_bitmax_tiles: bad arguments")
+        return out[:nt * self.n].reshape(nt, self.n)
+
     def warmup_freq(self, W: int, cut: int = 32) -> np.ndarray:
         f = np.empty(self.n, dtype=np.uint32)
         if _load().orc_pool_warmup_freq(self.h, W, cut, _p(f)) != 0:
             raise ValueError("warm-up block larger than the pool")
         return f
+
+
+def bitmax_query(tiles: np.ndarray, T: int, k: int):
+    """Algorithm 3 (POPCOUNT, argmax, SUBTRACT) over vertex-major tiles of
+    shape (ceil(T/32), n); the tiles are not modified."""
+    t = np.ascontiguousarray(tiles, dtype=np.uint32).copy()
+    n = t.shape[1]
+    seeds = np.empty(k, dtype=np.uint32)
+    marg = np.empty(k, dtype=np.uint64)
+    cov = ctypes.c_uint64()
+    if _load().orc_bitmax_query(n, T, _p(t), k, _p(seeds), _p(marg), ctypes.byref(cov)) != 0:
+        raise ValueError("orc_bitmax_query: bad arguments")
+    return seeds, marg, cov.value
+
+
+def huffmax_query(cb: "Codebook", encs, k: int):
+    """Algorithm 2 over encoded sets (dicts from encode_set)."""
+    T = len(encs)
+    kind = np.array([e["kind"] for e in encs], dtype=np.uint32)
+    ncod = np.array([e["n_coded"] for e in encs], dtype=np.uint32)
+    bits = np.array([e["code_bits"] for e in encs], dtype=np.uint64)
+    nraw = np.array([e["n_raw"] for e in encs], dtype=np.uint32)
+    blen = [len(e["bytes"]) for e in encs]
+    boff = np.concatenate([[0], np.cumsum(blen)]).astype(np.uint64)
+    roff = np.concatenate([[0], np.cumsum(nraw.astype(np.uint64))]).astype(np.uint64)
+    words = (cb.n + 31) // 32
+    bmoff = np.zeros(T, dtype=np.uint64)
+    bms = []
+    for j, e in enumerate(encs):
+        bmoff[j] = words * len(bms)
+        if e["kind"] == 1:
+            bms.append(_u32(e["bitmap"]))
+    by = np.frombuffer(b"".join(e["bytes"] for e in encs) + b"\0", dtype=np.uint8).copy()
+    raw = np.concatenate([_u32(e["raw"]) for e in encs] + [np.zeros(1, np.uint32)])
+    bm = np.concatenate(bms + [np.zeros(words, np.uint32)])
+    seeds = np.empty(k, dtype=np.uint32)
+    marg = np.empty(k, dtype=np.uint64)
+    cov = ctypes.c_uint64()
+    rc = _load().orc_huffmax_query(cb.n, _p(cb.len), _p(cb.code), T, _p(kind), _p(ncod), _p(bits), _p(boff[:T]),
+                                   _p(by), _p(nraw), _p(roff[:T]), _p(raw), _p(bmoff), _p(bm), k, _p(seeds),
+                                   _p(marg), ctypes.byref(cov))
+    if rc != 0:
+        raise ValueError("orc_huffmax_query: bad arguments or stream")
+    return seeds, marg, cov.value
 
 
 def greedy_lists(n: int, sets, k: int):

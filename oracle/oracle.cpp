@@ -699,4 +699,178 @@ int64_t orc_decode_set(uint32_t n, const uint32_t *len_of_v, const uint32_t *cod
     return (int64_t)s.size();
 }
 
+/* ------------------------------------------------------------------------- */
+/* Paper-literal modes (the results must equal the plain greedy's).           */
+/* ------------------------------------------------------------------------- */
+
+/* Exact argmax of a frequency table: the largest count, the lowest vertex id  */
+/* on ties, chosen vertices excluded (with every count 0 the lowest-id vertex  */
+/* not yet chosen).                                                            */
+static uint32_t argmax_unchosen(const std::vector<uint64_t> &h, const std::vector<uint8_t> &chosen) {
+    uint32_t n = (uint32_t)h.size(), best = n;
+    for (uint32_t v = 0; v < n; v++) {
+        if (chosen[v]) continue;
+        if (best == n || h[v] > h[best]) best = v;
+    }
+    return best;
+}
+
+/*
+ * Greedy with the frequency table rebuilt from scratch every iteration, as
+ * Algorithms 2 and 3 print it: h <- counts over the sets not yet covered;
+ * u* <- argmax h; every live set holding u* is deleted.  Exactly k seeds.
+ */
+int orc_pool_greedy_recount(void *hp, uint64_t T, uint32_t k, uint32_t *seeds, uint64_t *marginal,
+                            uint64_t *covered_out) {
+    orc_pool *p = (orc_pool *)hp;
+    uint32_t n = p->g.n;
+    if (T > p->sets.size() || k > n) return -1;
+    std::vector<uint8_t> alive(T, 1), chosen(n, 0);
+    uint64_t covered = 0;
+    for (uint32_t it = 0; it < k; it++) {
+        std::vector<uint64_t> h(n, 0);
+        for (uint64_t j = 0; j < T; j++)
+            if (alive[j])
+                for (uint32_t v : p->sets[j]) h[v]++;
+        uint32_t u = argmax_unchosen(h, chosen);
+        chosen[u] = 1;
+        seeds[it] = u;
+        uint64_t gain = 0;
+        for (uint64_t j = 0; j < T; j++) {
+            if (alive[j] && std::binary_search(p->sets[j].begin(), p->sets[j].end(), u)) {
+                alive[j] = 0;
+                gain++;
+            }
+        }
+        covered += gain;
+        if (marginal) marginal[it] = gain;
+    }
+    if (covered_out) *covered_out = covered;
+    return 0;
+}
+
+/*
+ * Characterize (Algorithm 1, first block): the skewness S (Eq. (2)) of the
+ * sizes of the warm-up sets [0, W) picks the scheme for the whole graph:
+ * Bitmax (every set a bitmap) when S < 0, else Huffmax (every set Huffman-
+ * coded, uncoded vertices in copy arrays).  Returns 1 for Bitmax, 0 for
+ * Huffmax, -1 on bad arguments; *skew_out gets S.
+ */
+int orc_pool_scheme(void *hp, uint64_t W, double *skew_out) {
+    orc_pool *p = (orc_pool *)hp;
+    if (W == 0 || W > p->sets.size()) return -1;
+    std::vector<uint64_t> sizes(W);
+    for (uint64_t j = 0; j < W; j++) sizes[j] = p->sets[j].size();
+    double skew = 0.0, density = 0.0;
+    orc_size_stats(sizes.data(), W, p->g.n, &skew, &density);
+    if (skew_out) *skew_out = skew;
+    return skew < 0.0 ? 1 : 0;
+}
+
+/*
+ * Bitmax block (Section 4.2.3) in the vertex-major form of Eq. (3): rows are
+ * vertices, columns are sets.  Tile t holds columns [32t, 32t + 32): word v of
+ * tile t (tiles[t * n + v]) has bit s set iff v is in set 32t + s; columns past
+ * T are zero.
+ */
+int orc_pool_bitmax_tiles(void *hp, uint64_t T, uint32_t *tiles) {
+    orc_pool *p = (orc_pool *)hp;
+    uint32_t n = p->g.n;
+    if (T > p->sets.size()) return -1;
+    uint64_t nt = (T + 31) / 32;
+    std::fill(tiles, tiles + nt * n, 0u);
+    for (uint64_t j = 0; j < T; j++)
+        for (uint32_t v : p->sets[j]) tiles[(j / 32) * n + v] |= 1u << (j % 32);
+    return 0;
+}
+
+/*
+ * BitmaxQuery (Algorithm 3; Eq. (3)) over vertex-major tiles: every iteration
+ * POPCOUNT gives each row's frequency, u* is the argmax over rows not yet
+ * chosen (deleteVTXflag), its popcount is the marginal gain, and every row v is
+ * replaced by SUBTRACT(v, u*) = v AND (v XOR u*), which clears the columns of
+ * the sets u* covers.  The tiles are modified in place.
+ */
+int orc_bitmax_query(uint32_t n, uint64_t T, uint32_t *tiles, uint32_t k, uint32_t *seeds, uint64_t *marginal,
+                     uint64_t *covered_out) {
+    if (k > n) return -1;
+    uint64_t nt = (T + 31) / 32;
+    std::vector<uint8_t> chosen(n, 0);
+    std::vector<uint32_t> urow(nt);
+    uint64_t covered = 0;
+    for (uint32_t it = 0; it < k; it++) {
+        std::vector<uint64_t> h(n, 0);
+        for (uint32_t v = 0; v < n; v++)
+            for (uint64_t t = 0; t < nt; t++) h[v] += (uint64_t)__builtin_popcount(tiles[t * n + v]);
+        uint32_t u = argmax_unchosen(h, chosen);
+        chosen[u] = 1;
+        seeds[it] = u;
+        for (uint64_t t = 0; t < nt; t++) urow[t] = tiles[t * n + u];
+        for (uint32_t v = 0; v < n; v++)
+            for (uint64_t t = 0; t < nt; t++) {
+                uint32_t x = tiles[t * n + v];
+                tiles[t * n + v] = x & (x ^ urow[t]);
+            }
+        covered += h[u];
+        if (marginal) marginal[it] = h[u];
+    }
+    if (covered_out) *covered_out = covered;
+    return 0;
+}
+
+/*
+ * HuffmaxDecodeQuery (Algorithm 2) over the encoded pool: each set j is given
+ * as its encoding (kind 0: n_coded codes in code_bits MSB-first bits of
+ * bytes[byte_off[j] ..], then n_raw copy-array ids at raw[raw_off[j] ..]; kind
+ * 1: a bitmap of ceil(n/32) words at bm[bm_off[j] ..]).  Every iteration the
+ * frequency table is rebuilt from the live sets: a live set is decoded; if it
+ * holds u* it is deleted, else its vertices are added to the table for the
+ * next iteration.  The first table counts every set.
+ */
+int orc_huffmax_query(uint32_t n, const uint32_t *len_of_v, const uint32_t *code_of_v, uint64_t T,
+                      const uint32_t *kind, const uint32_t *n_coded, const uint64_t *code_bits,
+                      const uint64_t *byte_off, const uint8_t *bytes, const uint32_t *n_raw,
+                      const uint64_t *raw_off, const uint32_t *raw, const uint64_t *bm_off, const uint32_t *bm,
+                      uint32_t k, uint32_t *seeds, uint64_t *marginal, uint64_t *covered_out) {
+    if (k > n) return -1;
+    std::vector<uint32_t> buf(n);
+    auto decode = [&](uint64_t j, std::vector<uint32_t> &out) -> bool {
+        int64_t sz = orc_decode_set(n, len_of_v, code_of_v, kind[j], n_coded[j], code_bits[j], bytes + byte_off[j],
+                                    raw + raw_off[j], n_raw[j], bm + bm_off[j], buf.data());
+        if (sz < 0) return false;
+        out.assign(buf.begin(), buf.begin() + sz);
+        return true;
+    };
+    std::vector<uint8_t> alive(T, 1), chosen(n, 0);
+    std::vector<uint64_t> h(n, 0);
+    std::vector<uint32_t> s;
+    for (uint64_t j = 0; j < T; j++) {
+        if (!decode(j, s)) return -2;
+        for (uint32_t v : s) h[v]++;
+    }
+    uint64_t covered = 0;
+    for (uint32_t it = 0; it < k; it++) {
+        uint32_t u = argmax_unchosen(h, chosen);
+        chosen[u] = 1;
+        seeds[it] = u;
+        std::vector<uint64_t> next(n, 0);
+        uint64_t gain = 0;
+        for (uint64_t j = 0; j < T; j++) {
+            if (!alive[j]) continue;
+            if (!decode(j, s)) return -2;
+            if (std::binary_search(s.begin(), s.end(), u)) {
+                alive[j] = 0;
+                gain++;
+            } else {
+                for (uint32_t v : s) next[v]++;
+            }
+        }
+        h.swap(next);
+        covered += gain;
+        if (marginal) marginal[it] = gain;
+    }
+    if (covered_out) *covered_out = covered;
+    return 0;
+}
+
 }  /* extern "C" */

@@ -7,13 +7,17 @@
   (1 - 1/e) guarantee against the best k-subset found by enumeration.
 - IMM's theta_i (Eq. (1), Section 2.2) against hand-worked values, and against
   the paper's printed form of Eq. (1) evaluated with scipy's log-gamma.
+- The paper-literal selection modes -- Algorithm 3's POPCOUNT / SUBTRACT query
+  over vertex-major tiles, Algorithm 2's decode query over encoded sets, the
+  per-iteration recount -- against Eq. (3)'s worked example and the greedy;
+  Algorithm 1's scheme switch against closed-form size distributions.
 """
 import itertools
 import math
 
 import numpy as np
 import pytest
-from scipy import special
+from scipy import special, stats
 
 import oracle
 import synth
@@ -171,3 +175,99 @@ def test_imm_estimate_close_to_brute_force_sigma():
                     stack.append(v)
         sigma += pr * len(seen)
     assert abs(r["influence"] - sigma) <= 0.3 * sigma
+
+
+# ---------------------------------------------------------------------------
+# paper-literal selection modes: Algorithm 3 over vertex-major tiles, Algorithm
+# 2 over encoded sets, and the per-iteration recount, against the worked
+# example of Eq. (3) and against the plain greedy
+# ---------------------------------------------------------------------------
+def _tiles_from_matrix(mat):
+    n, T = mat.shape
+    tiles = np.zeros(((T + 31) // 32, n), dtype=np.uint32)
+    for v in range(n):
+        for s in range(T):
+            if mat[v, s]:
+                tiles[s // 32, v] |= np.uint32(1 << (s % 32))
+    return tiles
+
+
+def test_bitmax_query_worked_example():
+    d = _golden_bitmax()
+    mat = np.array([[int(c) for c in row] for row in d["matrix"]])
+    n, T = mat.shape
+    seeds, marg, cov = oracle.bitmax_query(_tiles_from_matrix(mat), T, 2)
+    assert seeds.tolist() == [int(x) for x in d["seeds"][0].split()]
+    assert marg.tolist() == [int(x) for x in d["marginal"][0].split()]
+    assert cov == T
+    # k = 1 leaves exactly the SUBTRACT rows of Eq. (3): their popcounts pick v5
+    after = np.array([[int(c) for c in row] for row in d["after"]])
+    s1, m1, _ = oracle.bitmax_query(_tiles_from_matrix(mat), T, 1)
+    assert s1.tolist() == [0] and m1.tolist() == [int(mat[0].sum())]
+    assert int(np.argmax(after.sum(axis=1))) == int(seeds[1])
+
+
+def _small_pool(seed, T, p=0.1):
+    g = synth.rmat(512, 4096, seed)
+    g.prob = synth.ic_uniform(g, seed, p)
+    pool = oracle.Pool(g, oracle.IC, seed)
+    pool.extend(T)
+    return g, pool
+
+
+@pytest.mark.parametrize("seed,T,k", [(3, 100, 8), (4, 257, 20), (5, 64, 64)])
+def test_bitmax_tiles_layout(seed, T, k):
+    g, pool = _small_pool(seed, T)
+    tiles = pool.bitmax_tiles(T)
+    assert tiles.shape == ((T + 31) // 32, g.n)
+    for j in range(T):
+        members = set(pool.set(j).tolist())
+        col = (tiles[j // 32] >> np.uint32(j % 32)) & np.uint32(1)
+        assert set(np.nonzero(col)[0].tolist()) == members
+    # columns past T are zero
+    if T % 32:
+        assert not np.any(tiles[-1] >> np.uint32(T % 32))
+
+
+@pytest.mark.parametrize("seed,T,k,p", [(3, 100, 8, 0.1), (4, 257, 20, 0.1), (5, 64, 64, 0.1), (6, 300, 12, 0.3)])
+def test_literal_modes_equal_greedy(seed, T, k, p):
+    g, pool = _small_pool(seed, T, p)
+    ref = pool.greedy(T, k)
+    for got in (pool.greedy_recount(T, k), oracle.bitmax_query(pool.bitmax_tiles(T), T, k)):
+        assert got[0].tolist() == ref[0].tolist()
+        assert got[1].tolist() == ref[1].tolist() and got[2] == ref[2]
+    # Algorithm 2 over the encoded sets (codebook from the first quarter), for
+    # the per-set cut and for Huffmax (every set coded)
+    cb = oracle.Codebook(g.n, pool.warmup_freq(T // 4, 0))
+    for cut in (32, 0):
+        encs = [oracle.encode_set(cb, cut, pool.set(j)) for j in range(T)]
+        got = oracle.huffmax_query(cb, encs, k)
+        assert got[0].tolist() == ref[0].tolist()
+        assert got[1].tolist() == ref[1].tolist() and got[2] == ref[2]
+
+
+def test_scheme_switch_closed_forms():
+    """Algorithm 1's Characterize: Bitmax iff the warm-up sizes' skewness is
+    negative.  Star centre -> leaves with p = 1: a leaf's RR set is {leaf,
+    centre} (size 2) and the centre's is {centre} (size 1), so the sizes have
+    a long left tail (negative skew): Bitmax.  p = 0: every set is its root,
+    the sizes have no spread (skewness 0): Huffmax."""
+    n = 64
+    star = synth.from_edges(n, [(0, v) for v in range(1, n)], prob=[1.0] * (n - 1))
+    pool = oracle.Pool(star, oracle.IC, 3)
+    pool.extend(400)
+    sizes = pool.sizes(0, 400)
+    assert set(sizes.tolist()) == {1, 2} and (sizes == 1).any()
+    bitmax, sk = pool.scheme(400)
+    assert bitmax and sk < 0
+    assert abs(sk - stats.skew(sizes.astype(np.float64), bias=True)) < 1e-12
+    none = synth.from_edges(n, [(0, v) for v in range(1, n)], prob=[0.0] * (n - 1))
+    pool0 = oracle.Pool(none, oracle.IC, 3)
+    pool0.extend(100)
+    assert pool0.scheme(100) == (False, 0.0)
+    # a skewed pool (small sets with a few large ones) keeps Huffmax
+    g, pool2 = _small_pool(7, 400, 0.1)
+    bm2, sk2 = pool2.scheme(400)
+    s2 = pool2.sizes(0, 400).astype(np.float64)
+    assert abs(sk2 - stats.skew(s2, bias=True)) < 1e-9 * max(1.0, abs(sk2))
+    assert bm2 == (sk2 < 0)
