@@ -4,13 +4,22 @@
 One step = one whole IMM run through the library (sampling fused with Huffman /
 bitmap encoding for every estimation round and the final theta, greedy seed
 selection on the compressed pool each round, FP64 bounds), with the graph
-already resident in HBM.  Prints one JSON line (rank 0).
+already resident in HBM.  The default workload is the twitter7-sized IC graph
+(41,652,230 vertices, 1,468,365,182 edges, p ~ U[0, 0.1), k = 100, eps = 0.5).
+Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hbx|reference]
-                  [--workload wc_rmat1m] [--form 1] [--encode 1]
+                  [--workload ic_rmat42m] [--secondary wc_rmat1m] [--serving 200]
+
+Besides the timed steps the line carries: the same IMM end to end from host
+arrays (`e2e`), the plain one-launch-per-step form (`plain_form`), the
+weighted-cascade 2^20-vertex workload measured the same way (`secondary`), the
+serving stream (`serving`), the oracle on a bounded sample (`cpu_baseline`),
+and rooflines of the dominant kernels.  Optional legs that would push the run
+past --budget-s seconds are skipped and say so.
 
 `--impl reference` times the CPU oracle (the plain statement of the method) on
-the host cores, on a bounded sample of the same workload.  With N > 1 (torchrun)
+the host, on a bounded sample of the same workload.  With N > 1 (torchrun)
 every rank runs an independent replica (its own RR seed): the path has no data
 exchange between independent IM queries, so scaling is weak.
 """
@@ -19,6 +28,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -29,6 +39,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RR sets/s and end-to-end IMM s (bit-exact seeds); bytes/RR vertex; HBM GB/s % peak"
 UNIT = "RR sets/s"
+# workloads whose uncompressed (int32) pool would not fit one GPU: the plain
+# form's comparison leg runs with the same Huffman + bitmap encoding there
+INT32_TOO_BIG = {"ic_rmat42m"}
 
 
 def peaks():
@@ -38,6 +51,17 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
 
 
 class Clocks:
@@ -100,41 +124,92 @@ def graph_bytes(g):
     return b
 
 
-def oracle_sample_rate(g, w, target_s=15.0, budget_sets=None):
-    """Oracle throughput on a bounded sample: sample S sets of the workload on
-    all host cores, then greedy k on them; returns (sets/s, S, cores, seconds).
-    S is sized from a probe (doubling from 16 sets until a probe takes a
-    second) so that the measured leg takes about target_s."""
+# ---------------------------------------------------------------------------
+# oracle timing (the CPU baseline; test infrastructure, never on the product path)
+# ---------------------------------------------------------------------------
+def oracle_pool_rate(g, w, S, nthreads):
+    """Oracle: sample sets [0, S) on nthreads host threads, then greedy k on
+    them; returns (sets/s, seconds)."""
     import oracle
     model = oracle.IC if w.model == "IC" else oracle.LT
-    cores = os.cpu_count() or 1
-    S = budget_sets
-    if S is None:
-        probe_n = 16
-        while True:
-            probe = oracle.Pool(g, model, w.rr_seed)
-            t0 = time.perf_counter()
-            probe.extend(probe_n, cores)
-            probe.greedy(probe_n, w.k)
-            dt = time.perf_counter() - t0
-            del probe
-            if dt >= 1.0 or probe_n >= 2048:
-                break
-            probe_n *= 2
-        S = max(16, int(probe_n * target_s / max(dt, 1e-3)))
-        S = min(S, 2_000_000)
     pool = oracle.Pool(g, model, w.rr_seed)
     t0 = time.perf_counter()
-    pool.extend(S, cores)
+    pool.extend(S, nthreads)
     pool.greedy(S, w.k)
     dt = time.perf_counter() - t0
-    return S / dt, S, cores, dt
+    return S / dt, dt
+
+
+def oracle_sample_size(g, w, target_s, cores):
+    """Sets the oracle samples (with greedy) in about target_s on `cores`
+    threads: doubling from 16 sets until a probe takes a second."""
+    probe_n = 16
+    while True:
+        _, dt = oracle_pool_rate(g, w, probe_n, cores)
+        if dt >= 1.0 or probe_n >= 2048:
+            break
+        probe_n *= 2
+    return min(2_000_000, max(16, int(probe_n * target_s / max(dt, 1e-3))))
+
+
+def oracle_baseline(g, w, target_s=15.0):
+    cores = os.cpu_count() or 1
+    if w.name == "ic_rmat42m":
+        # a fifth of this graph's sets reach most of it (about 70 s each on one
+        # core): one set per core, all cores at once
+        S = cores
+    else:
+        S = oracle_sample_size(g, w, target_s, cores)
+    rate, dt = oracle_pool_rate(g, w, S, cores)
+    out = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": f"RR sets [0, {S}) of {w.name} sampled on {cores} threads, then greedy k={w.k} on them "
+                     f"({dt:.1f} s)"}
+    if w.name != "ic_rmat42m":
+        S1 = max(16, S // (4 * cores))
+        r1, d1 = oracle_pool_rate(g, w, S1, 1)
+        out["single_thread"] = {"value": r1, "unit": UNIT, "sample": f"RR sets [0, {S1}) then greedy, one thread "
+                                                                        f"({d1:.1f} s)"}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# rooflines
+# ---------------------------------------------------------------------------
+def sampler_roofline(stats, peak, peak_kind, wc):
+    """Sampling fused with encoding, by the per-set algorithmic bytes: 8 per
+    member (row_ptr pair), 4 per scanned edge for p (4 per member under the
+    weighted cascade, whose p is a function of the target), 4 per live edge
+    (col), plus the encoded bytes; over the sampling kernels' CUDA-event time."""
+    ksec = sum(s["sample_kernel_s"] for s in stats)
+    if ksec <= 0:
+        return None
+    per_p = (lambda s: 4 * s["rr_vertices"]) if wc else (lambda s: 4 * s["edges_scanned"])
+    alg = sum(8 * s["rr_vertices"] + per_p(s) + 4 * s["edges_live"] + s["pool_bytes"] for s in stats)
+    ach = alg / ksec / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "peak_kind": peak_kind, "kernel": "sampler: warp, shared-memory block and HBM block kernels, encode fused",
+            "launches": int(sum(s["sample_kernel_launches"] for s in stats)), "kernel_s": ksec,
+            "p_bytes": "4 per RR vertex (weighted cascade)" if wc else "4 per scanned edge"}
+
+
+def search_roofline(stats, ceiling):
+    """Bit-parallel search of the sets that outgrow shared memory: Philox
+    blocks drawn (one per edge group and set that still needed coins) over
+    the search's CUDA-event time, against the device's measured Philox rate."""
+    ksec = sum(s["ms_kernel_s"] for s in stats)
+    blocks = sum(s["ms_philox_blocks"] for s in stats)
+    if ksec <= 0 or not ceiling:
+        return None
+    ach = blocks / ksec / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": ceiling / 1e9, "unit": "G Philox4x32-10 blocks/s",
+            "frac": ach / (ceiling / 1e9), "traffic": None, "peak_kind": "measured (hbx_philox_ceiling)",
+            "kernel": "bit-parallel search (ms_light_kernel, ms_heavy_kernel, ms_compact_kernel per level)",
+            "kernel_s": ksec, "blocks": blocks, "sets": int(sum(s["ms_sets"] for s in stats))}
 
 
 def count_roofline(stats, peak):
-    """Achieved bandwidth of the selections' count passes (decoding or
-    bit-plane summing every counted set once): bytes they read over their
-    CUDA-event time."""
+    """Initial count passes (every counted set decoded or bit-plane summed once):
+    bytes they read over their CUDA-event time."""
     cs = sum(s["count_kernel_s"] for s in stats)
     cb = sum(s["count_bytes"] for s in stats)
     if cs <= 0:
@@ -143,6 +218,28 @@ def count_roofline(stats, peak):
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "bytes_per_step": cb / len(stats), "kernel_s_per_step": cs / len(stats),
             "kernel": "count_items_kernel + bitmap_count_kernel (+ count_raw_kernel)"}
+
+
+def dec_roofline(stats, peak):
+    """Decrement phases of the persistent selection: bytes of the covered sets
+    they read over their time (globaltimer, barrier to barrier)."""
+    ds = sum(s["dec_s"] for s in stats)
+    db = sum(s["dec_bytes"] for s in stats)
+    if ds <= 0:
+        return None
+    ach = db / ds / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "bytes_per_step": db / len(stats), "s_per_step": ds / len(stats),
+            "kernel": "select_persistent_kernel, decrement phase"}
+
+
+def selection_summary(stats):
+    it = sum(s["select_iterations"] for s in stats)
+    ks = sum(s["select_kernel_s"] for s in stats)
+    if it == 0:
+        return None
+    return {"iterations_per_step": it / len(stats), "us_per_iteration": 1e6 * ks / it,
+            "select_kernel_s_per_step": ks / len(stats)}
 
 
 def replica_seed(rr_seed, rank):
@@ -163,7 +260,78 @@ def reduce_over_ranks(total_ms, sets, device=None):
     return float(mx[0]), float(sm[1])
 
 
-def serving_leg(hbx, synth, tc, resident, count, rate=20.0, seed=3):
+def timed_imms(hbx, tc, G, w, seed, opts, steps, flush):
+    """`steps` IMMs, each bracketed by CUDA events on the library's stream, L2
+    flushed (a 512 MB write) before each, outside the interval."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, stats, r = [], [], None
+    for _ in range(steps):
+        with torch.cuda.stream(tc.stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        ev0.record(tc.stream)
+        r = hbx.hbx_imm(tc.ctx, G, w.model, w.k, w.eps, w.ell, seed, opts)
+        ev1.record(tc.stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        stats.append(r["stats"])
+    return ms, stats, r
+
+
+def pool_summary(s):
+    return {"theta": s["theta"], "rr_vertices": s["rr_vertices"],
+            "bytes_per_rr_vertex": s["pool_bytes"] / max(1, s["rr_vertices"]),
+            "compression_vs_int32": s["raw_int32_bytes"] / max(1, s["pool_bytes"]),
+            "uncoded_share": s["uncoded_vertices"] / max(1, s["rr_vertices"]),
+            "sets": {"huffman": s["sets_huffman"], "bitmap": s["sets_bitmap"], "raw": s["sets_raw"],
+                     "big": s["sets_big"], "bit_parallel": s["ms_sets"]},
+            "skewness": s["skewness"], "density": s["density"]}
+
+
+def plain_leg(hbx, tc, G, w, seed, steps, warmup, encode, flush, batched_ms, batched_r):
+    """The plain one-launch-per-step form on the same workload and seed."""
+    import numpy as np
+    import torch
+    torch.cuda.empty_cache()  # the plain form grows its heaps by copying (old + new at once)
+    popts = hbx.hbx_default_options(encode=encode, form=0)
+    for _ in range(warmup):
+        hbx.hbx_imm(tc.ctx, G, w.model, w.k, w.eps, w.ell, seed, popts)
+    pms, pstats, pr = timed_imms(hbx, tc, G, w, seed, popts, steps, flush)
+    pmean = sum(pms) / len(pms)
+    return {"ms_per_step": pmean, "value": pr["stats"]["theta"] / (pmean / 1000.0), "unit": UNIT,
+            "steps": steps, "warmup": warmup, "encode": "huffman+bitmap" if encode else "int32",
+            "batched_speedup": pmean / batched_ms, "seeds_equal": bool(np.array_equal(pr["seeds"], batched_r["seeds"])),
+            "influence_equal": pr["influence"] == batched_r["influence"],
+            "selection": selection_summary(pstats)}
+
+
+def secondary_leg(hbx, synth, tc, name, steps, warmup, flush, peak, peak_kind, with_cpu):
+    """A second workload measured the same way (timed IMMs, plain form,
+    rooflines), for the weighted-cascade graph whose sets are small."""
+    w = synth.WORKLOADS[name]
+    g = w.graph()
+    G = hbx.hbx_graph_create(tc.ctx, g)
+    opts = hbx.hbx_default_options(encode=1, form=1)
+    for _ in range(warmup):
+        hbx.hbx_imm(tc.ctx, G, w.model, w.k, w.eps, w.ell, w.rr_seed, opts)
+    ms, stats, r = timed_imms(hbx, tc, G, w, w.rr_seed, opts, steps, flush)
+    mean = sum(ms) / len(ms)
+    out = {"workload": name, "n": w.n, "m": w.m, "diffusion": w.model, "weights": w.weights, "k": w.k, "eps": w.eps,
+           "steps": steps, "warmup": warmup, "ms_per_step": mean, "value": stats[-1]["theta"] / (mean / 1000.0),
+           "unit": UNIT, **pool_summary(stats[-1]),
+           "roofline": sampler_roofline(stats, peak, peak_kind, w.weights == "wc"),
+           "count_roofline": count_roofline(stats, peak), "dec_roofline": dec_roofline(stats, peak),
+           "selection": selection_summary(stats),
+           "sample_kernel_s_per_step": sum(s["sample_kernel_s"] for s in stats) / len(stats)}
+    out["plain_form"] = plain_leg(hbx, tc, G, w, w.rr_seed, max(3, steps // 3), 1, 0, flush, mean, r)
+    if with_cpu:
+        out["cpu_baseline"] = oracle_baseline(g, w)
+    hbx.hbx_graph_destroy(G)
+    return out
+
+
+def serving_leg(hbx, synth, tc, count, rate=20.0, seed=3):
     """Poisson stream of IM queries over three resident graphs (the shapes of
     ic_rmat4k, wc_rmat1m and lt_rmat4m, each carrying IC probabilities and LT
     weights), model IC or LT, k in [10, 200], eps in {0.13, 0.2, 0.3, 0.5},
@@ -172,12 +340,13 @@ def serving_leg(hbx, synth, tc, resident, count, rate=20.0, seed=3):
     handles = []
     for name in ("ic_rmat4k", "wc_rmat1m", "lt_rmat4m"):
         w = synth.WORKLOADS[name]
-        g = resident.get(name) or w.graph()
+        g = w.graph()
         if g.lt_weight is None:
             g.lt_weight = synth.lt_weights(g, w.graph_seed)
         if g.prob is None:
             g.prob = synth.ic_uniform(g, w.graph_seed, 0.1)
         handles.append(hbx.hbx_graph_create(tc.ctx, g))
+        del g
     qs = synth.poisson_queries(seed=seed, count=count, rate_per_s=rate, graphs=[0, 1, 2])
     srv = hbx.hbx_server_create(tc.ctx, 4, 0)
     lat, fails = [], 0
@@ -202,9 +371,10 @@ def serving_leg(hbx, synth, tc, resident, count, rate=20.0, seed=3):
         for h in handles:
             hbx.hbx_graph_destroy(h)
     lat = np.array(lat) if lat else np.zeros(1)
-    return {"queries": count, "failed": fails, "rate_per_s": rate, "queries_per_s": (count - fails) / wall,
-            "wall_s": wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_inflight": 4,
+    qps = (count - fails) / wall
+    return {"queries": count, "failed": fails, "rate_per_s": rate, "queries_per_s": qps, "wall_s": wall,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_inflight": 4, "keeps_up": qps >= 0.95 * rate,
             "graphs": "ic_rmat4k, wc_rmat1m, lt_rmat4m shapes (IC probabilities and LT weights on each)"}
 
 
@@ -212,74 +382,79 @@ def run_reference(args, rank):
     import synth
     if rank != 0:
         return
+    import oracle
     w = synth.WORKLOADS[args.workload]
     g = w.graph()
-    rates = []
-    S = None
-    cores = os.cpu_count() or 1
-    for i in range(args.warmup + args.steps):
-        rate, S, cores, dt = oracle_sample_rate(g, w, target_s=min(15.0, 120.0 / max(1, args.steps + args.warmup)),
-                                                budget_sets=S)
-        if i >= args.warmup:
-            rates.append((rate, dt))
-    tot_sets = S * len(rates)
-    tot_t = sum(dt for _, dt in rates)
-    value = tot_sets / tot_t
-    sample = f"{S} RR sets of {w.name} sampled (all host cores) then greedy k={w.k} on them, per step"
+    model = oracle.IC if w.model == "IC" else oracle.LT
+    times = []
+    if w.name == "ic_rmat42m":
+        # one RR set per step on one thread (set id = step index): a fifth of
+        # this graph's sets take about a minute each, so a step of one set per
+        # core would take a minute almost every time
+        cores = 1
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oracle.rr_set(g, model, w.rr_seed, 0, i)
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        S = 1
+        sample = (f"one RR set of {w.name} per step (set id = step index, ids {args.warmup}..{args.warmup + args.steps - 1} "
+                  f"timed), one thread")
+    else:
+        cores = os.cpu_count() or 1
+        S = oracle_sample_size(g, w, min(15.0, 120.0 / max(1, args.steps + args.warmup)), cores)
+        for i in range(args.warmup + args.steps):
+            _, dt = oracle_pool_rate(g, w, S, cores)
+            if i >= args.warmup:
+                times.append(dt)
+        sample = f"RR sets [0, {S}) of {w.name} sampled on {cores} threads then greedy k={w.k} on them, per step"
+    tot_t = sum(times)
+    value = S * len(times) / tot_t
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / len(rates),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "m": w.m, "diffusion": w.model, "weights": w.weights, "k": w.k,
-                   "eps": w.eps, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+                   "eps": w.eps, "ell": w.ell, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 def run_hbx(args, rank, world, local_rank):
-    import numpy as np
     import torch
 
     import paper_2208_00613_gb300 as hbx
     import synth
 
+    t_start = time.perf_counter()
     dist = world > 1
     if dist:
         import torch.distributed as tdist
     torch.cuda.set_device(local_rank)
     hbx.build()
     w = synth.WORKLOADS[args.workload]
+    t0 = time.perf_counter()
     g = w.graph()
+    synth_s = time.perf_counter() - t0
     seed = replica_seed(w.rr_seed, rank)
     tc = hbx.torch_context(local_rank)
     ctx = tc.ctx
     G = hbx.hbx_graph_create(ctx, g)
     opts = hbx.hbx_default_options(encode=args.encode, form=args.form)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local_rank}")
-
-    def one_step():
-        return hbx.hbx_imm(ctx, G, w.model, w.k, w.eps, w.ell, seed, opts)
+    peak, peak_kind = peaks()
+    ceiling = hbx.hbx_philox_ceiling(ctx)
 
     for _ in range(args.warmup):
-        one_step()
+        hbx.hbx_imm(ctx, G, w.model, w.k, w.eps, w.ell, seed, opts)
     torch.cuda.synchronize()
     if dist:
         tdist.barrier()
     clocks = Clocks(local_rank)
     clocks.start()
-    step_ms, stats = [], []
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.steps):
-        with torch.cuda.stream(tc.stream):
-            flush.zero_()  # L2 flush between timed steps, outside the timed interval
-        torch.cuda.synchronize()
-        ev0.record(tc.stream)
-        r = one_step()
-        ev1.record(tc.stream)
-        ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        stats.append(r["stats"])
+    step_ms, stats, r = timed_imms(hbx, tc, G, w, seed, opts, args.steps, flush)
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = sum(step_ms)
@@ -289,20 +464,20 @@ def run_hbx(args, rank, world, local_rank):
     else:
         total_ms_all, sets_all = total_ms, float(sets)
     value = sets_all / (total_ms_all / 1000.0)
+    imm_ms = total_ms / args.steps
 
     # end to end through the C ABI from host buffers: graph upload, IMM, results back
-    e2e_ms = []
+    e2e_ms, e2e_sets = [], 0
     h2d = graph_bytes(g)
     d2h = w.k * 4 + w.k * 8 + 8 + ctypes_sizeof_stats(hbx)
-    e2e_sets = 0
-    for _ in range(max(1, args.steps // 2)):
+    for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G2 = hbx.hbx_graph_create(ctx, g)
-        r = hbx.hbx_imm(ctx, G2, w.model, w.k, w.eps, w.ell, seed, opts)
+        r2 = hbx.hbx_imm(ctx, G2, w.model, w.k, w.eps, w.ell, seed, opts)
         hbx.hbx_graph_destroy(G2)
         e2e_ms.append(1000 * (time.perf_counter() - t0))
-        e2e_sets += r["stats"]["theta"]
+        e2e_sets += r2["stats"]["theta"]
     e2e_value = e2e_sets / (sum(e2e_ms) / 1000.0)
 
     if rank != 0:
@@ -310,85 +485,78 @@ def run_hbx(args, rank, world, local_rank):
             tdist.barrier()
         tc.close()
         return
-    # the plain one-launch-per-step form (int32 sets, block per set, selection
-    # launched round by round) on the same workload and seed, same timing rules
-    plain = None
-    if not args.no_plain and args.form == 1:
-        # return the batched pools' memory, cached by torch's allocator, to the
-        # device: the plain form grows its heaps by copying (old + new at once)
-        torch.cuda.empty_cache()
-        popts = hbx.hbx_default_options(encode=args.plain_encode, form=0)
-        for _ in range(args.plain_warmup):
-            hbx.hbx_imm(ctx, G, w.model, w.k, w.eps, w.ell, seed, popts)
-        pms, pr = [], None
-        for _ in range(args.steps):
-            with torch.cuda.stream(tc.stream):
-                flush.zero_()
-            torch.cuda.synchronize()
-            ev0.record(tc.stream)
-            pr = hbx.hbx_imm(ctx, G, w.model, w.k, w.eps, w.ell, seed, popts)
-            ev1.record(tc.stream)
-            ev1.synchronize()
-            pms.append(ev0.elapsed_time(ev1))
-        pmean = sum(pms) / len(pms)
-        plain = {"ms_per_step": pmean, "value": pr["stats"]["theta"] / (pmean / 1000.0), "unit": UNIT,
-                 "encode": "huffman+bitmap" if args.plain_encode else "int32",
-                 "batched_speedup": pmean / (total_ms / args.steps), "warmup": args.plain_warmup,
-                 "seeds_equal": bool(np.array_equal(pr["seeds"], r["seeds"])),
-                 "influence_equal": pr["influence"] == r["influence"]}
+
+    def left():
+        return args.budget_s - (time.perf_counter() - t_start)
+
+    skipped = {}
+    secondary = None
+    if args.secondary and world == 1:
+        if left() > 120:
+            secondary = secondary_leg(hbx, synth, tc, args.secondary, 12, 3, flush, peak, peak_kind,
+                                      not args.no_cpu_baseline)
+        else:
+            skipped["secondary"] = "time budget"
     serving = None
     if args.serving:
-        serving = serving_leg(hbx, synth, tc, {w.name: g}, args.serving)
-    # roofline of the dominant kernel (sampling fused with encoding)
-    peak, peak_kind = peaks()
-    alg_bytes = sum(8 * s["rr_vertices"] + 4 * s["edges_scanned"] + 4 * s["edges_live"] + s["pool_bytes"]
-                    for s in stats)
-    ksec = sum(s["sample_kernel_s"] for s in stats)
-    klaunch = sum(s["sample_kernel_launches"] for s in stats)
-    achieved = alg_bytes / ksec / 1e9 if ksec > 0 else 0.0
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "sample_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                pj = json.load(f)
-            if pj.get("workload") == w.name and pj.get("source_hash") == source_hash():
-                traffic = pj.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
-    s0 = stats[-1]
+        if left() > 240:
+            serving = serving_leg(hbx, synth, tc, args.serving)
+        else:
+            skipped["serving"] = "time budget"
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, S, cores, dt = oracle_sample_rate(g, w)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{S} RR sets of {w.name} sampled then greedy k={w.k} on them ({dt:.1f} s)"}
+        if left() > 200:
+            cpu = oracle_baseline(g, w)
+        else:
+            skipped["cpu_baseline"] = "time budget"
+    plain = None
+    if not args.no_plain and args.form == 1:
+        enc = args.plain_encode if args.plain_encode >= 0 else (1 if w.name in INT32_TOO_BIG else 0)
+        pw = args.plain_warmup if args.plain_warmup >= 0 else (0 if w.name in INT32_TOO_BIG else 1)
+        # the plain form ran about 5x slower than the batched one at full size
+        if left() > 10 * imm_ms / 1000.0 * (args.plain_steps + pw) + 30:
+            plain = plain_leg(hbx, tc, G, w, seed, args.plain_steps, pw, enc, flush, imm_ms, r)
+        else:
+            skipped["plain_form"] = "time budget"
+
+    s0 = stats[-1]
+    search = search_roofline(stats, ceiling)
+    samp = sampler_roofline(stats, peak, peak_kind, w.weights == "wc")
+    # the dominant kernel: the bit-parallel search when it holds most of the
+    # sampling time, else the sampler as a whole
+    dominant = search if search and search["kernel_s"] > 0.5 * samp["kernel_s"] else samp
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "m": w.m, "diffusion": w.model, "weights": w.weights, "k": w.k,
                    "eps": w.eps, "ell": w.ell, "encode": "huffman+bitmap" if args.encode else "int32",
-                   "form": "persistent+graph" if args.form else "plain", "parallelism": f"replicas{world}",
+                   "form": "persistent" if args.form else "plain", "parallelism": f"replicas{world}",
                    "l2": "flushed (512 MB write) between timed steps"},
         "imm_s": total_ms_all / args.steps / 1000.0,
-        "theta": s0["theta"], "rr_vertices": s0["rr_vertices"],
-        "bytes_per_rr_vertex": s0["pool_bytes"] / max(1, s0["rr_vertices"]),
-        "compression_vs_int32": s0["raw_int32_bytes"] / max(1, s0["pool_bytes"]),
+        **pool_summary(s0),
         "traversed_edges_per_s": sum(s["edges_scanned"] for s in stats) / (total_ms / 1000.0),
-        "sets": {"huffman": s0["sets_huffman"], "bitmap": s0["sets_bitmap"], "raw": s0["sets_raw"],
-                 "big": s0["sets_big"]},
-        "skewness": s0["skewness"], "density": s0["density"], "warp_capacity": s0["warp_capacity"],
+        "warp_capacity": s0["warp_capacity"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
+                "ms_per_step": sum(e2e_ms) / len(e2e_ms), "steps": len(e2e_ms)},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "sampler: warp, shared-memory block and HBM block kernels, encode fused",
-                     "launches": klaunch, "kernel_s": ksec},
+        "roofline": dominant,
+        "sampler_roofline": samp,
+        "search_roofline": search,
         "count_roofline": count_roofline(stats, peak),
+        "dec_roofline": dec_roofline(stats, peak),
+        "selection": selection_summary(stats),
+        "phase_s_per_step": {"sample_kernels": sum(s["sample_kernel_s"] for s in stats) / len(stats),
+                             "bit_parallel_search": sum(s["ms_kernel_s"] for s in stats) / len(stats),
+                             "count": sum(s["count_kernel_s"] for s in stats) / len(stats),
+                             "select_iterations": sum(s["select_kernel_s"] for s in stats) / len(stats)},
         "cpu_baseline": cpu,
         "plain_form": plain,
+        "secondary": secondary,
         "serving": serving,
+        "skipped": skipped or None,
+        "synth_s": synth_s,
+        "wall_s": time.perf_counter() - t_start,
         "clocks": clk,
     }
     print(json.dumps(out), flush=True)
@@ -402,33 +570,28 @@ def ctypes_sizeof_stats(hbx):
     return ctypes.sizeof(hbx.hbx_stats)
 
 
-def source_hash():
-    """Hash of the sampler kernels' sources (their device code and launchers):
-    a stored DRAM-traffic capture is used only while these are unchanged."""
-    import hashlib
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2208_00613_gb300", "csrc")
-    for f in ("common.cuh", "internal.h", "sample.cu", "msbfs.cu"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hbx", choices=["hbx", "reference"])
-    ap.add_argument("--workload", default="wc_rmat1m")
+    ap.add_argument("--workload", default="ic_rmat42m")
     ap.add_argument("--form", type=int, default=1)
     ap.add_argument("--encode", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison leg")
-    ap.add_argument("--serving", type=int, default=0, help="queries of the serving leg (0: skip)")
-    ap.add_argument("--plain-warmup", type=int, default=1, help="untimed plain-form IMMs before its timed ones")
-    ap.add_argument("--plain-encode", type=int, default=0,
-                    help="encoding of the plain-form leg (1 where an int32 pool would not fit the GPU)")
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--plain-warmup", type=int, default=-1,
+                    help="untimed plain-form IMMs before its timed ones (-1: 0 at full size, else 1)")
+    ap.add_argument("--plain-encode", type=int, default=-1,
+                    help="encoding of the plain-form leg (-1: Huffman + bitmap where an int32 pool would not fit "
+                         "the GPU, else int32)")
+    ap.add_argument("--secondary", default="wc_rmat1m", help="second workload measured in the same run ('' = none)")
+    ap.add_argument("--serving", type=int, default=200, help="queries of the serving leg (0: skip)")
+    ap.add_argument("--budget-s", type=float, default=1500.0,
+                    help="optional legs that would run past this many seconds are skipped")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

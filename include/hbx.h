@@ -50,7 +50,7 @@ enum {
     HBX_ERR_INVALID_ARG = -1,  /* bad size, id, probability, option or handle */
     HBX_ERR_OOM = -2,          /* device allocation failed or over max_device_bytes */
     HBX_ERR_CUDA = -3,         /* a CUDA call failed; message in hbx_last_error */
-    HBX_ERR_TIMEOUT = -4,      /* a bounded wait ran out (hbx_wait) */
+    HBX_ERR_TIMEOUT = -4,      /* a bounded wait ran out (hbx_wait, or a device-side wait) */
     HBX_ERR_WEIGHTS_GT_1 = -5, /* an LT vertex's in-weights sum above 1 */
     HBX_ERR_ADMISSION = -6,    /* a served query can never fit the memory budget */
     HBX_ERR_CANCELLED = -7,    /* a served query was cancelled */
@@ -75,7 +75,7 @@ typedef struct {
      * the k selection rounds launched one by one with a host read-back after
      * each; 1: persistent work-stealing warp kernel with shared-memory and
      * HBM block tiers for the sets that outgrow it, fused with encoding, and
-     * the k selection rounds replayed from one CUDA graph. */
+     * the k selection rounds in one persistent cooperative launch. */
     uint32_t form;
     /* Philox counter word 2 of every draw; pools with different epochs are
      * independent.  Default 0. */
@@ -92,6 +92,26 @@ typedef struct {
     uint32_t block_cluster;
     /* Upper bound on the device bytes of one pool; 0 = no bound. */
     uint64_t max_device_bytes;
+    /* Longest a device-side wait may last, in SM clock cycles (the grid
+     * barriers of the batched form's selection); a wait that runs out ends the
+     * call with TIMEOUT and leaves the context usable.  0 = 4e9 (about 2 s). */
+    uint64_t wait_cycles;
+    /* Encoding scheme of an encoded pool.  0: per set, by density_cut (a set
+     * is a bitmap iff c * |R| > n).  1: per graph, as Algorithm 1's
+     * Characterize does: the skewness S (Eq. (2)) of the warm-up block's set
+     * sizes picks Bitmax (every set a bitmap) when S < 0, else Huffmax (every
+     * set Huffman-coded, density_cut ignored).  A Bitmax IC pool stores its
+     * sets as the vertex-major bit matrix of Section 4.2.3 / Eq. (3): tiles of
+     * 32 consecutive sets, word v of a tile holding bit s for set 32t + s; it
+     * samples every set with the bit-parallel search. */
+    uint32_t scheme;
+    /* Greedy counting of the batched form.  0: count once, then decrement the
+     * covered sets' vertices each iteration.  1: rebuild the counts from the
+     * sets not yet covered every iteration, as Algorithms 2 and 3 print it
+     * (Bitmax tiles: POPCOUNT of each row under the live-set mask, i.e. after
+     * Eq. (3)'s SUBTRACT).  The seeds are the same either way; the plain form
+     * always decrements. */
+    uint32_t select_mode;
 } hbx_options;
 
 typedef struct {
@@ -100,8 +120,10 @@ typedef struct {
     uint64_t sets_huffman, sets_bitmap, sets_raw;
     uint64_t sets_big;         /* sets sampled by a whole block (> warp capacity) */
     uint64_t rr_vertices;      /* sum of |R_j| over the pool */
-    uint64_t edges_scanned;    /* in-edges whose coin was drawn (IC) or whose weight was read (LT) */
-    uint64_t edges_live;
+    uint64_t edges_scanned;    /* in-edges of the sets' members (IC) or weights read (LT) */
+    uint64_t edges_live;       /* live in-edges found; for IC sets searched bit-parallel (those
+                                  that outgrow shared memory) only the live edges into sources
+                                  not yet in the set at the edge's BFS level */
     uint64_t pool_bytes;       /* index + code + copy + bitmap heaps in use */
     uint64_t raw_int32_bytes;  /* 4 * rr_vertices + 8 * theta: the uncompressed pool */
     uint64_t code_bits;        /* Huffman payload bits */
@@ -127,6 +149,23 @@ typedef struct {
      * set record, 8 per chunk item and 4 per bitmap-list entry */
     double count_kernel_s;
     uint64_t count_bytes;
+    /* the bit-parallel search of the IC sets that outgrow shared memory:
+     * device time of its batches (levels, tally, emit), sets searched, and
+     * Philox blocks drawn (one per edge group and set that needed coins) */
+    double ms_kernel_s;
+    uint64_t ms_sets;
+    uint64_t ms_philox_blocks;
+    /* greedy iterations of the selections: device time (CUDA events around
+     * them, the initial count excluded), iterations run, and for the batched
+     * form the time of their decrement phases and the bytes those read (code
+     * bytes and items of the covered Huffman sets' chunks, copy-array ids,
+     * covered bitmap rows) */
+    double select_kernel_s;
+    uint64_t select_iterations;
+    double dec_s;
+    uint64_t dec_bytes;
+    /* vertex occurrences of Huffman sets stored in copy arrays (no code) */
+    uint64_t uncoded_vertices;
 } hbx_stats;
 
 /* Human-readable name of an HBX_ERR_* code. */
@@ -286,6 +325,17 @@ int hbx_cancel(hbx_ticket *t);
 void hbx_ticket_destroy(hbx_ticket *t);
 
 /*
+ * Measurement aid (the paper has no counterpart): the device's rate of
+ * Philox4x32-10 blocks -- the arithmetic that bounds the bit-parallel search
+ * of the sets that outgrow shared memory -- with every thread drawing blocks
+ * back to back and touching no memory but one output word.  Best of three
+ * timed launches on the context's stream after one warm-up launch.
+ *   blocks_per_s  out: Philox blocks per second.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int hbx_philox_ceiling(hbx_ctx *ctx, double *blocks_per_s);
+
+/*
  * Allocation-free argmax over a device array of counts.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device
  * memory where they need it -- a service that reserves all of its GPU memory up
@@ -294,16 +344,23 @@ void hbx_ticket_destroy(hbx_ticket *t);
  * allocator.  It runs the selection's argmax (largest count, lowest id on
  * ties; any int32 values) but keeps its scratch (per-block partial maxima and a
  * finish counter, 32 KB) in a static device array that every device loading
- * the library holds until the process exits.  It calls no allocation routine.
+ * the library holds until the process exits.  It calls no allocation routine
+ * (see the set-up below).
  *   d_counts  device pointer, n int32 counts, on the current device.
  *   n         1 .. HBX_ARGMAX_NOALLOC_MAX; larger n fails with INVALID_ARG.
  *   d_out     device pointer to one uint32: the winning index, written when the
  *             stream reaches the launch (the call does not synchronise).
  *   stream    cudaStream_t of the current device (NULL = legacy default stream).
- * The first call on a device looks up the scratch array's device address (once
- * per device, with that device current).  All calls on a device share the
- * array: calls whose launches overlap on the GPU race and must be ordered by
- * the caller (one stream, or events).  Errors: INVALID_ARG, CUDA.
+ * The first call on a device does a one-time set-up with that device current:
+ * it loads the library's device code on that device (CUDA loads modules lazily,
+ * and loading reserves device memory for the code and the 32 KB array) and
+ * looks up the scratch array's device address.  Only the calls after it are
+ * allocation-free, so make the first call before the memory budget is
+ * reserved and before any stream capture.  A call with d_counts == NULL,
+ * n == 0 and d_out == NULL does only that set-up and launches nothing.  All
+ * calls on a device share the array: calls whose launches overlap on the GPU
+ * race and must be ordered by the caller (one stream, or events).
+ * Errors: INVALID_ARG, CUDA.
  */
 #define HBX_ARGMAX_NOALLOC_MAX 16777216u
 int hbx_argmax_noalloc(const int32_t *d_counts, uint32_t n, uint32_t *d_out, void *stream);

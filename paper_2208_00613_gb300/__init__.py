@@ -37,7 +37,8 @@ class hbx_options(ctypes.Structure):
     _fields_ = [("density_cut", ctypes.c_uint32), ("warmup_sets", ctypes.c_uint32), ("encode", ctypes.c_uint32),
                 ("form", ctypes.c_uint32), ("pool_epoch", ctypes.c_uint32), ("warp_capacity", ctypes.c_uint32),
                 ("warp_group_budget", ctypes.c_uint32), ("block_cluster", ctypes.c_uint32),
-                ("max_device_bytes", ctypes.c_uint64)]
+                ("max_device_bytes", ctypes.c_uint64), ("wait_cycles", ctypes.c_uint64),
+                ("scheme", ctypes.c_uint32), ("select_mode", ctypes.c_uint32)]
 
 
 class hbx_stats(ctypes.Structure):
@@ -49,7 +50,10 @@ class hbx_stats(ctypes.Structure):
                [(f, ctypes.c_double) for f in ["lb", "sample_s", "select_s", "total_s", "skewness", "density",
                                                 "sample_kernel_s"]] + \
                [("sample_kernel_launches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("count_kernel_s", ctypes.c_double), ("count_bytes", ctypes.c_uint64)]
+                ("count_kernel_s", ctypes.c_double), ("count_bytes", ctypes.c_uint64),
+                ("ms_kernel_s", ctypes.c_double), ("ms_sets", ctypes.c_uint64), ("ms_philox_blocks", ctypes.c_uint64),
+                ("select_kernel_s", ctypes.c_double), ("select_iterations", ctypes.c_uint64),
+                ("dec_s", ctypes.c_double), ("dec_bytes", ctypes.c_uint64), ("uncoded_vertices", ctypes.c_uint64)]
 
     def to_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -99,6 +103,7 @@ def lib():
         "hbx_cancel": (I, [P]),
         "hbx_ticket_destroy": (None, [P]),
         "hbx_argmax_noalloc": (I, [P, U32, P, P]),
+        "hbx_philox_ceiling": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -301,6 +306,13 @@ def hbx_cancel(ticket) -> int:
 
 def hbx_ticket_destroy(ticket):
     lib().hbx_ticket_destroy(ticket)
+
+
+def hbx_philox_ceiling(ctx) -> float:
+    """Philox4x32-10 blocks per second of the device (see include/hbx.h)."""
+    out = ctypes.c_double()
+    _check(lib().hbx_philox_ceiling(ctx, ctypes.byref(out)), ctx)
+    return out.value
 
 
 def hbx_argmax_noalloc(d_counts: int, n: int, d_out: int, stream: int | None = None) -> int:

@@ -93,7 +93,8 @@ struct Counters {
     unsigned long long raw_fail, code_fail, bm_fail;
     // histogram passes: sets at or above the density cut, vertices of the others
     unsigned long long hist_dense, hist_verts;
-    unsigned long long pad[5];
+    unsigned long long uncoded;  // vertices of Huffman sets stored in copy arrays
+    unsigned long long pad[4];
 };
 
 struct SampleArgs {
@@ -124,6 +125,8 @@ struct SampleArgs {
     uint32_t* bp_queue;       // slots x n
     uint32_t* bp_aux;         // slots x bp_words
     uint64_t bp_words;        // ceil(n/32) rounded up to 4
+    uint32_t* sizes;          // MODE_HIST: sizes[j] = |R_j| for j < sizes_cap (or null)
+    uint32_t sizes_cap;
 };
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,7 @@ struct MsCounters {
     unsigned long long size[MS_SETS];     // per set of the batch
     unsigned long long scanned[MS_SETS];
     unsigned long long live[MS_SETS];
+    unsigned long long blocks;  // Philox blocks drawn for the batch
 };
 
 struct MsArgs {
@@ -40,6 +41,8 @@ struct MsArgs {
     Counters* ctr;
     SetRec* recs;
     const unsigned long long* rowoff;  // [MS_SETS] bitmap-heap word offset of each dense set's row
+    uint32_t* sizes;                   // histogram passes: sizes[j] = |R_j| for j < sizes_cap (or null)
+    uint32_t sizes_cap;
 };
 
 // roots of the batch, compacted into the first frontier
@@ -55,6 +58,11 @@ cudaError_t launch_ms_finish(const MsArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_ms_emit(const MsArgs& a, uint32_t dense, uint32_t mode, uint64_t row_words, uint32_t* bm_heap,
                            int sms, cudaStream_t s);
 
+// Philox4x32-10 blocks drawn back to back by `blocks` x 256 threads,
+// `per_thread` each (the ALU ceiling of the bit-parallel search); out: one
+// word per thread.
+cudaError_t launch_philox_ceiling(uint32_t blocks, uint32_t per_thread, uint32_t* out, cudaStream_t s);
+
 // sets of a bit-parallel batch under the density cut, encoded one block each
 // (scratch slot b for the b-th listed set)
 cudaError_t launch_ms_sparse(const SampleArgs& a, const uint32_t* vis, const uint32_t* sbits, const uint32_t* ids,
@@ -68,6 +76,8 @@ struct SelState {
     unsigned long long gain;     // sets covered by u* this iteration
     unsigned long long covered;  // total covered
     unsigned long long n_dec;    // chunk items of the Huffman sets covered this iteration
+    unsigned long long dec_bytes;  // bytes read by the decrement passes (code bytes, copy ids, items, rows)
+    unsigned long long t_argmax_ns, t_cover_ns, t_dec_ns;  // persistent selection: phase times (globaltimer)
 };
 
 struct SelArgs {
@@ -97,6 +107,7 @@ struct SelArgs {
     uint32_t* seeds;                       // [k]
     unsigned long long* marginal;          // [k]
     int sms;
+    long long wait_cycles;                 // bound of every grid-barrier wait
 };
 
 constexpr uint32_t HOT_RANKS = 12288;  // ranks privatised in shared memory by the count kernel
@@ -113,6 +124,16 @@ cudaError_t launch_count(const SelArgs& a, uint32_t encode, cudaStream_t s);
 // one greedy iteration: argmax, cover test, decrements, finalize
 cudaError_t launch_iteration(const SelArgs& a, uint32_t encode, cudaStream_t s);
 cudaError_t launch_argmax(const SelArgs& a, cudaStream_t s);
+
+// Grid barrier of the persistent selection (zeroed before each launch).
+struct SelBarrier {
+    unsigned int count, gen, err, pad;
+};
+// All k greedy iterations in one cooperative launch (argmax, cover, decrement
+// separated by bounded grid barriers); bar->err != 0 afterwards means a
+// barrier wait ran out.  select_persistent_blocks: its grid (0: cannot run).
+cudaError_t launch_select_persistent(const SelArgs& a, uint32_t k, SelBarrier* bar, cudaStream_t s);
+int select_persistent_blocks(int sms);
 
 // ---- pool indexing and inspection (select.cu) ----
 struct IndexArgs {

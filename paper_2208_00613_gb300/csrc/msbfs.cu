@@ -7,21 +7,26 @@
 // bit per set: vis[v] and nxt[v] are 32-bit masks (visited; reached during
 // this level), and the frontier lists each vertex once per level with the
 // mask of the sets whose frontier holds it.  A vertex's in-edge probabilities
-// and sources are then read once for all of those sets, and each set still
-// draws its own coin for every in-edge of every vertex it visits, so the sets
-// and their scanned and live edge counts are those of one search per set.
+// and sources are then read once for all of those sets.  A set draws its coins
+// for a group of 4 in-edges only while one of their sources is still unvisited
+// in that set (a visited source cannot join it again), so the sets equal those
+// of one full search per set; their scanned-edge counts are those of the full
+// search (every in-edge of every member), while their live-edge counts cover
+// only the live edges into sources not yet visited at the edge's level.
 //
 // A level is: the light kernel takes the frontier 32 vertices per warp (edge
 // groups spread over the lanes by a warp prefix sum; vertices with more than
 // MS_HEAVY groups are cut into chunks of MS_CHUNK groups for the heavy
-// kernel, which spreads them over whole blocks); every live edge ORs its sets
-// into nxt[source] with a reduction that returns nothing, so no thread waits
-// on it; then the compaction pass turns nxt into the next frontier, keeping
-// for each vertex only the sets that had not visited it yet (marking them in
-// vis), and clears nxt.  The host advances levels until the frontier is empty,
-// then a tally pass gives each set's size and scanned edges, and the emit pass
-// writes the dense sets' bitmap rows (a 32 x 32 bit transpose per warp through
-// shared memory) and clears vis for the next batch.
+// kernel); in both, a warp stages 32 groups at a time, finds the sets that
+// still need each group's coins, and spreads those (group, set) pairs evenly
+// over its lanes, one Philox block each.  Every live edge ORs its sets into
+// nxt[source] with a reduction that returns nothing, so no thread waits on it;
+// then the compaction pass turns nxt into the next frontier, keeping for each
+// vertex only the sets that had not visited it yet (marking them in vis), and
+// clears nxt.  The host advances levels until the frontier is empty, then a
+// tally pass gives each set's size and scanned edges, and the emit pass writes
+// the dense sets' bitmap rows (a 32 x 32 bit transpose per warp through shared
+// memory) and clears vis for the next batch.
 #include <cstdint>
 
 #include "common.cuh"
@@ -46,69 +51,105 @@ __device__ __forceinline__ void ms_init_shared(const MsArgs& a, uint32_t* s_sets
     __syncthreads();
 }
 
-__device__ __forceinline__ void ms_flush_live(const MsArgs& a, uint32_t (*s_live)[MS_SETS]) {
+__device__ __forceinline__ void ms_flush_live(const MsArgs& a, uint32_t (*s_live)[MS_SETS], uint32_t nblk) {
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncwarp();
     const uint32_t c = s_live[warp][lane];
     if (c) atomicAdd(&a.mc->live[lane], (unsigned long long)c);
+    if (lane == 0 && nblk) atomicAdd(&a.mc->blocks, (unsigned long long)nblk);
 }
 
-// The probabilities and sources of one aligned group of 4 in-edges.
-struct MsGroupData {
-    uint4 p;  // live thresholds
-    uint4 c;  // sources
+// One warp's staging of a round: up to 32 aligned groups of 4 in-edges, one
+// per lane, and for each the sets that still need its coins.
+struct MsRound {
+    uint4 thr[32];      // live thresholds of the group's edges
+    uint4 um[32];       // per edge: sets of the frontier mask whose source is not yet visited
+    uint4 em[32];       // per edge: sets for which it is live (filled by the items)
+    uint32_t gg[32];    // group index (the Philox counter's first word)
+    uint32_t need[32];  // union of the group's um: one Philox block per set in it
+    uint32_t scan[32];  // inclusive prefix sum of popc(need) over the slots
 };
 
-__device__ __forceinline__ MsGroupData ms_load(const MsArgs& a, uint32_t gg) {
-    MsGroupData d;
-    d.p = __ldg(reinterpret_cast<const uint4*>(a.g.thr) + gg);
-    d.c = __ldg(reinterpret_cast<const uint4*>(a.col4) + gg);
-    return d;
+// Position of the r-th (from 0) set bit of m, which has more than r set bits.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
+    uint32_t pos = 0, c = __popc(m & 0xFFFFu);
+    if (r >= c) { r -= c; m >>= 16; pos += 16; }
+    c = __popc(m & 0xFFu);
+    if (r >= c) { r -= c; m >>= 8; pos += 8; }
+    c = __popc(m & 0xFu);
+    if (r >= c) { r -= c; m >>= 4; pos += 4; }
+    c = __popc(m & 0x3u);
+    if (r >= c) { r -= c; m >>= 2; pos += 2; }
+    if (r >= (m & 1u)) pos += 1;
+    return pos;
 }
 
-// Coins of set s on group gg: bit k of the result is edge 4gg+k's.
-__device__ __forceinline__ uint32_t ms_coins(const MsArgs& a, const MsGroupData& d, uint32_t gg, uint32_t j,
-                                             uint32_t vm) {
-    const uint4 x = philox4x32_10(make_uint4(gg, j, a.epoch, STREAM_IC), a.key0, a.key1);
-    return vm & ((uint32_t)ic_live(x.x, d.p.x) | ((uint32_t)ic_live(x.y, d.p.y) << 1) |
-                 ((uint32_t)ic_live(x.z, d.p.z) << 2) | ((uint32_t)ic_live(x.w, d.p.w) << 3));
-}
-
-// Group gg of a frontier vertex whose in-edges are [eb, ee), for the sets in
-// mask f (two sets' Philox blocks at a time, which are independent); each
-// live edge ORs its sets into nxt[source] with one reduction.
-__device__ __forceinline__ void ms_group(const MsArgs& a, const uint32_t* s_sets, uint32_t* s_live_w,
-                                         const MsGroupData& d, uint32_t gg, uint32_t eb, uint32_t ee, uint32_t f) {
-    const uint32_t e0 = gg * 4u;
-    const uint32_t vm = (uint32_t)(e0 >= eb && e0 < ee) | ((uint32_t)(e0 + 1 >= eb && e0 + 1 < ee) << 1) |
-                        ((uint32_t)(e0 + 2 >= eb && e0 + 2 < ee) << 2) | ((uint32_t)(e0 + 3 >= eb && e0 + 3 < ee) << 3);
-    uint32_t em0 = 0, em1 = 0, em2 = 0, em3 = 0;  // sets for which edge 4gg+k is live
-    while (f) {
-        const uint32_t s1 = __ffs(f) - 1;
-        f &= f - 1;
-        const uint32_t s2 = f ? __ffs(f) - 1 : s1;
-        f &= f - 1;
-        const uint32_t c1 = ms_coins(a, d, gg, s_sets[s1], vm);
-        const uint32_t c2 = s2 != s1 ? ms_coins(a, d, gg, s_sets[s2], vm) : 0u;
-        if (c1) {
-            atomicAdd(&s_live_w[s1], (uint32_t)__popc(c1));
-            em0 |= (c1 & 1u) << s1;
-            em1 |= ((c1 >> 1) & 1u) << s1;
-            em2 |= ((c1 >> 2) & 1u) << s1;
-            em3 |= ((c1 >> 3) & 1u) << s1;
-        }
-        if (c2) {
-            atomicAdd(&s_live_w[s2], (uint32_t)__popc(c2));
-            em0 |= (c2 & 1u) << s2;
-            em1 |= ((c2 >> 1) & 1u) << s2;
-            em2 |= ((c2 >> 2) & 1u) << s2;
-            em3 |= ((c2 >> 3) & 1u) << s2;
+// One round of a warp.  Lane l brings group gg of a frontier vertex whose
+// in-edges are [eb, ee), for the sets of mask f (valid = false: no group).
+// A set needs the group's Philox block only if the source of one of the
+// vertex's edges in the group has not been visited by that set: a visited
+// source cannot join the set again, so its coin decides nothing.  The (group,
+// set) pairs that remain are spread evenly over the lanes, one Philox block
+// each; live edges into unvisited sources are collected per edge in shared
+// memory and then ORed into nxt[source] with one reduction per edge.
+__device__ __forceinline__ void ms_round(const MsArgs& a, MsRound& R, const uint32_t* s_sets, uint32_t* s_live_w,
+                                         uint32_t& nblk, bool valid, uint32_t gg, uint32_t eb, uint32_t ee,
+                                         uint32_t f) {
+    const uint32_t lane = threadIdx.x & 31;
+    uint4 c = make_uint4(0, 0, 0, 0), um = make_uint4(0, 0, 0, 0), thr = make_uint4(0, 0, 0, 0);
+    if (valid && f) {
+        c = __ldg(reinterpret_cast<const uint4*>(a.col4) + gg);
+        const uint32_t e0 = gg * 4u;
+        if (e0 >= eb && e0 < ee) um.x = f & ~__ldg(a.vis + c.x);
+        if (e0 + 1 >= eb && e0 + 1 < ee) um.y = f & ~__ldg(a.vis + c.y);
+        if (e0 + 2 >= eb && e0 + 2 < ee) um.z = f & ~__ldg(a.vis + c.z);
+        if (e0 + 3 >= eb && e0 + 3 < ee) um.w = f & ~__ldg(a.vis + c.w);
+    }
+    const uint32_t need = um.x | um.y | um.z | um.w;
+    if (need) thr = __ldg(reinterpret_cast<const uint4*>(a.g.thr) + gg);
+    const uint32_t incl = warp_incl_scan((uint32_t)__popc(need));
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (total == 0) return;  // warp-uniform
+    nblk += total;  // one Philox block per (group, set) pair
+    R.thr[lane] = thr;
+    R.um[lane] = um;
+    R.em[lane] = make_uint4(0, 0, 0, 0);
+    R.gg[lane] = gg;
+    R.need[lane] = need;
+    R.scan[lane] = incl;
+    __syncwarp();
+    for (uint32_t t = lane; t < total; t += 32) {
+        // slot = number of slots whose inclusive count is <= t
+        uint32_t slot = 0;
+#pragma unroll
+        for (uint32_t step = 16; step; step >>= 1)
+            if (R.scan[slot + step - 1] <= t) slot += step;
+        const uint32_t nd = R.need[slot];
+        const uint32_t r = t - (R.scan[slot] - (uint32_t)__popc(nd));
+        const uint32_t s = nth_set_bit(nd, r);
+        const uint4 x = philox4x32_10(make_uint4(R.gg[slot], s_sets[s], a.epoch, STREAM_IC), a.key0, a.key1);
+        const uint4 th = R.thr[slot], u = R.um[slot];
+        const uint32_t bit = 1u << s;
+        const bool l0 = (u.x & bit) && ic_live(x.x, th.x);
+        const bool l1 = (u.y & bit) && ic_live(x.y, th.y);
+        const bool l2 = (u.z & bit) && ic_live(x.z, th.z);
+        const bool l3 = (u.w & bit) && ic_live(x.w, th.w);
+        if (l0 | l1 | l2 | l3) {
+            uint32_t* em = reinterpret_cast<uint32_t*>(&R.em[slot]);
+            if (l0) atomicOr(em + 0, bit);
+            if (l1) atomicOr(em + 1, bit);
+            if (l2) atomicOr(em + 2, bit);
+            if (l3) atomicOr(em + 3, bit);
+            atomicAdd(&s_live_w[s], (uint32_t)l0 + (uint32_t)l1 + (uint32_t)l2 + (uint32_t)l3);
         }
     }
-    if (em0) atomicOr(&a.nxt[d.c.x], em0);
-    if (em1) atomicOr(&a.nxt[d.c.y], em1);
-    if (em2) atomicOr(&a.nxt[d.c.z], em2);
-    if (em3) atomicOr(&a.nxt[d.c.w], em3);
+    __syncwarp();
+    const uint4 em = R.em[lane];
+    if (em.x) atomicOr(&a.nxt[c.x], em.x);
+    if (em.y) atomicOr(&a.nxt[c.y], em.y);
+    if (em.z) atomicOr(&a.nxt[c.z], em.z);
+    if (em.w) atomicOr(&a.nxt[c.w], em.w);
+    __syncwarp();  // the staging is reused by the next round
 }
 
 // Roots of the batch's sets, reached at level 0.  <<<1, 32>>>
@@ -125,11 +166,13 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
     __shared__ uint32_t s_live[MS_WARPS][MS_SETS];
     __shared__ uint32_t w_scan[MS_WARPS][32], w_g0[MS_WARPS][32], w_eb[MS_WARPS][32], w_ee[MS_WARPS][32],
         w_f[MS_WARPS][32];
+    __shared__ MsRound s_round[MS_WARPS];
     const uint32_t nF = a.mc->nF;
     if (blockIdx.x * MS_WARPS * 32 >= nF) return;  // thin level: this block has no chunk
     ms_init_shared(a, s_sets, s_live);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * MS_WARPS * 32;
+    uint32_t nblk = 0;
     for (uint32_t c = (blockIdx.x * MS_WARPS + warp) * 32; c < nF; c += stride) {
         const uint32_t i = c + lane;
         uint32_t v = 0, f = 0, b = 0, e = 0, gfirst = 0, ng = 0;
@@ -143,7 +186,7 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
                 ng = ((e - 1) >> 2) - gfirst + 1;
             }
             if (ng > MS_HEAVY) {
-                // heavy vertex: its groups go to whole blocks in chunks
+                // heavy vertex: its groups go to whole warps in chunks
                 for (uint32_t g = gfirst; g < gfirst + ng; g += MS_CHUNK) {
                     const uint32_t h = atomicAdd(&a.mc->nH, 1u);
                     if (h < a.heavy_cap) a.heavy[h] = make_uint4(v, g, min(g + MS_CHUNK, gfirst + ng), f);
@@ -160,35 +203,44 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
         w_ee[warp][lane] = e;
         w_f[warp][lane] = f;
         __syncwarp();
-        for (uint32_t t = lane; t < total; t += 32) {
-            uint32_t lo = 0, hi = 31;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (w_scan[warp][mid] > t) hi = mid;
-                else lo = mid + 1;
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t t = base + lane;
+            uint32_t gg = 0, eb = 0, ee = 0, ff = 0;
+            if (t < total) {
+                uint32_t lo = 0, hi = 31;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (w_scan[warp][mid] > t) hi = mid;
+                    else lo = mid + 1;
+                }
+                gg = w_g0[warp][lo] + (t - (lo ? w_scan[warp][lo - 1] : 0u));
+                eb = w_eb[warp][lo];
+                ee = w_ee[warp][lo];
+                ff = w_f[warp][lo];
             }
-            const uint32_t gg = w_g0[warp][lo] + (t - (lo ? w_scan[warp][lo - 1] : 0u));
-            ms_group(a, s_sets, s_live[warp], ms_load(a, gg), gg, w_eb[warp][lo], w_ee[warp][lo], w_f[warp][lo]);
+            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, t < total, gg, eb, ee, ff);
         }
         __syncwarp();
     }
-    ms_flush_live(a, s_live);
+    ms_flush_live(a, s_live, nblk);
 }
 
-__global__ void __launch_bounds__(MS_THREADS) ms_heavy_kernel(MsArgs a) {
+__global__ void __launch_bounds__(MS_THREADS, 4) ms_heavy_kernel(MsArgs a) {
     __shared__ uint32_t s_sets[MS_SETS];
     __shared__ uint32_t s_live[MS_WARPS][MS_SETS];
+    __shared__ MsRound s_round[MS_WARPS];
     const uint32_t nH = min(a.mc->nH, a.heavy_cap);
     if (blockIdx.x * MS_WARPS >= nH) return;
     ms_init_shared(a, s_sets, s_live);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t nblk = 0;
     for (uint32_t it = blockIdx.x * MS_WARPS + warp; it < nH; it += gridDim.x * MS_WARPS) {
         const uint4 item = a.heavy[it];  // one chunk per warp
         const uint32_t eb = __ldg(a.g.row_ptr + item.x), ee = __ldg(a.g.row_ptr + item.x + 1);
-        for (uint32_t gg = item.y + lane; gg < item.z; gg += 32)
-            ms_group(a, s_sets, s_live[warp], ms_load(a, gg), gg, eb, ee, item.w);
+        for (uint32_t g = item.y; g < item.z; g += 32)
+            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, g + lane < item.z, g + lane, eb, ee, item.w);
     }
-    ms_flush_live(a, s_live);
+    ms_flush_live(a, s_live, nblk);
 }
 
 // The vertices reached during the level, with the sets that had not visited
@@ -312,6 +364,8 @@ __global__ void ms_commit_kernel(MsArgs a, uint32_t dense, uint32_t mode, uint64
     const uint32_t s = threadIdx.x;
     const bool d = (dense >> s) & 1u;
     unsigned long long verts = 0, sc = 0, lv = 0;
+    if (mode == MODE_HIST && s < a.mc->nsets && a.sizes && a.sets[s] < a.sizes_cap)
+        a.sizes[a.sets[s]] = (uint32_t)a.mc->size[s];
     if (d && mode == MODE_ENCODE) {
         a.recs[a.sets[s]] = make_rec(KIND_BITMAP, a.rowoff[s], (uint32_t)a.mc->size[s], 0);
         verts = a.mc->size[s];
@@ -380,6 +434,32 @@ cudaError_t launch_ms_emit(const MsArgs& a, uint32_t dense, uint32_t mode, uint6
                            int sms, cudaStream_t s) {
     ms_emit_kernel<<<(uint32_t)sms * 2, MS_THREADS, 0, s>>>(a, mode == MODE_ENCODE ? dense : 0u, bm_heap);
     ms_commit_kernel<<<1, 32, 0, s>>>(a, dense, mode, row_words);
+    return cudaGetLastError();
+}
+
+}  // namespace hbx
+
+// ---------------------------------------------------------------------------
+// Philox throughput ceiling: every thread draws `per_thread` blocks back to
+// back (distinct counters, the search's key) and folds them into one word, so
+// the kernel does nothing but the bit-parallel search's arithmetic.  Its rate
+// is the ALU roofline of that search.
+// ---------------------------------------------------------------------------
+namespace hbx {
+
+__global__ void __launch_bounds__(256) philox_ceiling_kernel(uint32_t per_thread, uint32_t key0, uint32_t key1,
+                                                             uint32_t* out) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < per_thread; i++) {
+        const uint4 x = philox4x32_10(make_uint4(i, tid, 0u, STREAM_IC), key0, key1);
+        acc ^= x.x ^ x.y ^ x.z ^ x.w;
+    }
+    out[tid] = acc;
+}
+
+cudaError_t launch_philox_ceiling(uint32_t blocks, uint32_t per_thread, uint32_t* out, cudaStream_t s) {
+    philox_ceiling_kernel<<<blocks, 256, 0, s>>>(per_thread, 0x243F6A88u, 0x85A308D3u, out);
     return cudaGetLastError();
 }
 

@@ -129,6 +129,9 @@ extern "C" void hbx_default_options(hbx_options* o) {
     o->warp_group_budget = 0;
     o->block_cluster = 0;
     o->max_device_bytes = 0;
+    o->wait_cycles = 0;
+    o->scheme = 0;
+    o->select_mode = 0;
 }
 
 extern "C" int hbx_create(hbx_ctx** out, int dev, void* stream) {
@@ -487,6 +490,8 @@ static SampleArgs sample_args(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t 
     a.bp_queue = p->bp_queue;
     a.bp_aux = p->bp_aux;
     a.bp_words = p->bp_words;
+    a.sizes = p->wsizes;
+    a.sizes_cap = p->wsizes_cap;
     return a;
 }
 
@@ -565,6 +570,8 @@ static MsArgs ms_args(hbx_pool* p) {
     a.ctr = p->ctr;
     a.recs = p->recs;
     a.rowoff = p->ms_rowoff;
+    a.sizes = p->wsizes;
+    a.sizes_cap = p->wsizes_cap;
     return a;
 }
 
@@ -625,6 +632,10 @@ static int run_multi_source(hbx_pool* p, uint32_t mode, uint32_t cut, const std:
         MsCounters mc;
         CK(cudaMemcpyAsync(&mc, p->ms_c, sizeof(mc), cudaMemcpyDeviceToHost, p->stream));
         CK(cudaStreamSynchronize(p->stream));
+        if (timed) {
+            p->ms_nsets += nb;
+            p->ms_blocks += mc.blocks;
+        }
         uint32_t dense = 0, nd = 0, nsp = 0;
         unsigned long long rowoff[MS_SETS] = {0};
         uint32_t sparse[2 * MS_SETS];  // mask bits, then set ids, of the sets under the cut
@@ -662,6 +673,7 @@ static int run_multi_source(hbx_pool* p, uint32_t mode, uint32_t cut, const std:
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
             p->sample_kernel_s += ms * 1e-3;
+            p->ms_kernel_s += ms * 1e-3;
             p->sample_kernel_launches++;
         }
     }
@@ -950,6 +962,44 @@ static int choose_shape(hbx_pool* p, Shape* out) {
     return HBX_OK;
 }
 
+// Characterize (Algorithm 1, first block): the skewness S of the warm-up sets'
+// sizes (Eq. (2), population standard deviation, the sizes summed in set
+// order) picks Bitmax (every set a bitmap: cut n + 1) when S < 0, else Huffmax
+// (every set coded: cut 0).  A Bitmax IC pool keeps its sets as vertex-major
+// tiles of 32 sets.
+static int characterize(hbx_pool* p) {
+    hbx_ctx* ctx = p->ctx;
+    const uint64_t W = p->wsizes_cap;
+    std::vector<uint32_t> sz(W);
+    CK(cudaMemcpyAsync(sz.data(), p->wsizes, W * 4, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    double sum = 0.0;
+    for (uint64_t i = 0; i < W; i++) sum += (double)sz[i];
+    const double mean = sum / (double)W;
+    double m2 = 0.0, m3 = 0.0;
+    for (uint64_t i = 0; i < W; i++) {
+        const double d = (double)sz[i] - mean;
+        m2 += d * d;
+        m3 += d * d * d;
+    }
+    m2 /= (double)W;
+    m3 /= (double)W;
+    p->scheme_skew = m2 > 0.0 ? m3 / (m2 * std::sqrt(m2)) : 0.0;
+    p->bitmax = p->scheme_skew < 0.0;
+    const uint32_t n = p->g->n;
+    if (p->bitmax) {
+        p->cut = n + 1;
+        p->tiles = p->model == HBX_IC;
+        p->hist_dense = W;
+        p->hist_verts = 0;
+    } else {
+        p->cut = 0;
+        p->hist_dense = 0;
+        p->hist_verts = (uint64_t)sum;
+    }
+    return HBX_OK;
+}
+
 static int ensure_codebook(hbx_pool* p) {
     hbx_ctx* ctx = p->ctx;
     if (!p->o.encode || p->has_cb) return HBX_OK;
@@ -960,7 +1010,14 @@ static int ensure_codebook(hbx_pool* p) {
     RC(grow_buffer(p, (void**)&freq, 0, (size_t)n * 4, 0));
     const unsigned long long sc0 = p->hc.edges_scanned, lv0 = p->hc.edges_live;
     const unsigned long long hd0 = p->hc.hist_dense, hv0 = p->hc.hist_verts;
-    int r = run_sample(p, MODE_HIST, 0, (uint32_t)p->W, nullptr, freq, p->o.density_cut, p->shape);
+    // the per-graph scheme (Algorithm 1) counts every warm-up set (Huffmax
+    // codes all of them) and records the sizes for Characterize
+    if (p->o.scheme) {
+        p->cut = 0;
+        RC(grow_buffer(p, (void**)&p->wsizes, 0, (size_t)p->W * 4, 0));
+        p->wsizes_cap = (uint32_t)p->W;
+    }
+    int r = run_sample(p, MODE_HIST, 0, (uint32_t)p->W, nullptr, freq, p->cut, p->shape);
     p->aux_scanned += p->hc.edges_scanned - sc0;
     p->aux_live += p->hc.edges_live - lv0;
     p->hist_sets = p->W;
@@ -974,6 +1031,13 @@ static int ensure_codebook(hbx_pool* p) {
     }
     dfree(ctx, freq);
     p->device_bytes -= (size_t)n * 4;
+    if (!r && p->o.scheme) r = characterize(p);
+    if (p->wsizes) {
+        dfree(ctx, p->wsizes);
+        p->device_bytes -= (size_t)p->wsizes_cap * 4;
+        p->wsizes = nullptr;
+        p->wsizes_cap = 0;
+    }
     if (r) return r;
     return build_codebook(p, hf);
 }
@@ -1011,6 +1075,13 @@ static int reserve_heaps(hbx_pool* p, uint64_t count) {
     return HBX_OK;
 }
 
+// Sets [j0, j0 + count) of a Bitmax IC pool as vertex-major tiles.
+static int run_tiles(hbx_pool* p, uint32_t j0, uint32_t count) {
+    (void)j0;
+    (void)count;
+    return fail(p->ctx, HBX_ERR_INVALID_ARG, "vertex-major tiles: not available");
+}
+
 int pool_extend(hbx_pool* p, uint64_t T) {
     hbx_ctx* ctx = p->ctx;
     if (T <= p->T) return HBX_OK;
@@ -1027,7 +1098,8 @@ int pool_extend(hbx_pool* p, uint64_t T) {
         const uint32_t count = (uint32_t)std::min<uint64_t>(T - j0, batch_max);
         const unsigned long long verts_before = p->hc.rr_vertices;
         RC(reserve_heaps(p, count));
-        RC(run_sample(p, mode, (uint32_t)j0, count, nullptr, nullptr, p->o.density_cut, p->shape));
+        if (p->tiles) RC(run_tiles(p, (uint32_t)j0, count));
+        else RC(run_sample(p, mode, (uint32_t)j0, count, nullptr, nullptr, p->cut, p->shape));
         // selection index of the new sets
         const uint64_t added = p->hc.rr_vertices - verts_before;
         const uint64_t items_need = p->hc.chunk_items + added / 32 + 2ull * count + 16;
@@ -1125,12 +1197,19 @@ static SelArgs sel_args(hbx_pool* p, uint64_t T) {
     a.seeds = p->d_seeds;
     a.marginal = p->d_marg;
     a.sms = p->ctx->sms;
+    a.wait_cycles = p->o.wait_cycles ? (long long)std::min<uint64_t>(p->o.wait_cycles, 1ull << 62) : 4000000000ll;
     return a;
 }
 
+// The persistent selection's grid barrier lives in the pool's small counter
+// allocation, after the argmax finish counter.
+static SelBarrier* sel_barrier(hbx_pool* p) {
+    return reinterpret_cast<SelBarrier*>(reinterpret_cast<char*>(p->ticket) + 64);
+}
+
 // Launch greedy selection on sets [0, T) on stream `st` without waiting.  The
-// persistent form replays the k iterations from one CUDA graph; the plain form
-// launches them one by one and reads u* back after each.
+// batched form runs the k iterations in one persistent cooperative launch; the
+// plain form launches them one by one and reads u* back after each.
 static int pool_select_launch(hbx_pool* p, uint64_t T, uint32_t k, cudaStream_t st) {
     hbx_ctx* ctx = p->ctx;
     if (T == 0 || T > p->T) return fail(ctx, HBX_ERR_INVALID_ARG, "T must be in [1, pool size]");
@@ -1160,6 +1239,8 @@ static int pool_select_launch(hbx_pool* p, uint64_t T, uint32_t k, cudaStream_t 
     if (!p->evc0) {
         CK(cudaEventCreate(&p->evc0));
         CK(cudaEventCreate(&p->evc1));
+        CK(cudaEventCreate(&p->evs0));
+        CK(cudaEventCreate(&p->evs1));
     }
     CK(cudaEventRecord(p->evc0, st));
     CK(launch_count(c, enc, st));
@@ -1177,32 +1258,24 @@ static int pool_select_launch(hbx_pool* p, uint64_t T, uint32_t k, cudaStream_t 
         p->base_T = T;
     }
     const uint64_t per_it = 3 + (enc ? (uint64_t)(a.has_cb ? 1 : 0) + (a.n_bm ? 1 : 0) : 1);
-    p->launches += 1 + (enc ? (uint64_t)((a.n_items && a.has_cb) ? 1 : 0) + (a.n_bm ? 1 : 0) : 1) + per_it * k;
+    p->launches += 1 + (enc ? (uint64_t)((a.n_items && a.has_cb) ? 1 : 0) + (a.n_bm ? 1 : 0) : 1);
+    CK(cudaEventRecord(p->evs0, st));
     if (p->o.form) {
-        cudaGraph_t graph;
-        cudaGraphExec_t exec;
-        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        cudaError_t le = cudaSuccess;
-        for (uint32_t it = 0; it < k && le == cudaSuccess; it++) le = launch_iteration(a, enc, st);
-        cudaError_t ce = cudaStreamEndCapture(st, &graph);
-        if (le != cudaSuccess) return cuda_fail(ctx, le, "selection capture");
-        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
-        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-        if (ie != cudaSuccess) {
-            cudaGraphDestroy(graph);
-            return cuda_fail(ctx, ie, "cudaGraphInstantiate");
-        }
-        cudaError_t le2 = cudaGraphLaunch(exec, st);
-        cudaGraphExecDestroy(exec);  // released once the launched work completes
-        cudaGraphDestroy(graph);
-        if (le2 != cudaSuccess) return cuda_fail(ctx, le2, "cudaGraphLaunch");
+        // all k iterations in one cooperative launch with bounded grid barriers
+        SelBarrier* bar = sel_barrier(p);
+        CK(cudaMemsetAsync(bar, 0, sizeof(SelBarrier), st));
+        CK(launch_select_persistent(a, k, bar, st));
+        p->launches += 1;
+        CK(cudaEventRecord(p->evs1, st));
     } else {
+        p->launches += per_it * k;
         SelState hs;
         for (uint32_t it = 0; it < k; it++) {
             CK(launch_iteration(a, enc, st));
             CK(cudaMemcpyAsync(&hs, a.st, sizeof(SelState), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
         }
+        CK(cudaEventRecord(p->evs1, st));
     }
     return HBX_OK;
 }
@@ -1216,13 +1289,21 @@ static int pool_select_finish(hbx_pool* p, uint32_t k, uint32_t* seeds, uint64_t
     CK(cudaMemcpyAsync(&hs, p->st, sizeof(SelState), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(seeds, p->d_seeds, (size_t)k * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hm.data(), p->d_marg, (size_t)k * 8, cudaMemcpyDeviceToHost, st));
+    SelBarrier hb = {0, 0, 0, 0};
+    if (p->o.form) CK(cudaMemcpyAsync(&hb, sel_barrier(p), sizeof(hb), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (hb.err) return fail(ctx, HBX_ERR_TIMEOUT, "selection: a grid barrier wait ran out");
     if (p->count_pending) {
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, p->evc0, p->evc1));
         p->count_kernel_s += ms * 1e-3;
+        CK(cudaEventElapsedTime(&ms, p->evs0, p->evs1));
+        p->select_kernel_s += ms * 1e-3;
         p->count_pending = false;
     }
+    p->select_iterations += hs.it;
+    p->dec_bytes += hs.dec_bytes;
+    p->dec_s += 1e-9 * (double)hs.t_dec_ns;
     if (hs.pad == 1) return fail(ctx, HBX_ERR_INTERNAL, "undecodable Huffman stream during selection");
     if (hs.pad) return fail(ctx, HBX_ERR_INTERNAL, "decrement item list overflow during selection");
     if (hs.it != k) return fail(ctx, HBX_ERR_INTERNAL, "selection ran " + std::to_string(hs.it) + " iterations");
@@ -1259,6 +1340,9 @@ extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint
         return fail(ctx, HBX_ERR_INVALID_ARG, "warp_capacity must be a power of two in [64, 2048]");
     if (o.block_cluster > 8 || (o.block_cluster & (o.block_cluster - 1)))
         return fail(ctx, HBX_ERR_INVALID_ARG, "block_cluster must be 0, 1, 2, 4 or 8");
+    if (o.scheme > 1 || o.select_mode > 1) return fail(ctx, HBX_ERR_INVALID_ARG, "scheme and select_mode are 0 or 1");
+    if (o.scheme && !o.encode) return fail(ctx, HBX_ERR_INVALID_ARG, "the per-graph scheme needs encode = 1");
+    if (g->n >= 0xFFFFFFFFu && o.scheme) return fail(ctx, HBX_ERR_INVALID_ARG, "graph too large for the Bitmax cut");
     cudaSetDevice(ctx->device);
     hbx_pool* p = new hbx_pool();
     p->ctx = ctx;
@@ -1267,6 +1351,7 @@ extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint
     p->seed = seed;
     p->o = o;
     p->W = o.warmup_sets;
+    p->cut = o.density_cut;
     p->stream = ctx->stream;
     p->bp_words = (((uint64_t)g->n + 31) / 32 + 3) & ~3ull;
     int r = grow_buffer(p, (void**)&p->ctr, 0, sizeof(Counters), 0);
@@ -1303,6 +1388,8 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
     if (p->ms_first) cudaGraphExecDestroy(p->ms_first);
     if (p->ms_more) cudaGraphExecDestroy(p->ms_more);
     if (p->evc0) cudaEventDestroy(p->evc0);
+    if (p->evs0) cudaEventDestroy(p->evs0);
+    if (p->evs1) cudaEventDestroy(p->evs1);
     if (p->evc1) cudaEventDestroy(p->evc1);
     if (p->own_stream) cudaStreamDestroy(p->stream);
     {
@@ -1409,6 +1496,14 @@ void fill_stats(hbx_pool* p, hbx_stats* s) {
     s->kernel_launches = p->launches;
     s->count_kernel_s = p->count_kernel_s;
     s->count_bytes = p->count_bytes;
+    s->ms_kernel_s = p->ms_kernel_s;
+    s->ms_sets = p->ms_nsets;
+    s->ms_philox_blocks = p->ms_blocks;
+    s->select_kernel_s = p->select_kernel_s;
+    s->select_iterations = p->select_iterations;
+    s->dec_s = p->dec_s;
+    s->dec_bytes = p->dec_bytes;
+    s->uncoded_vertices = p->hc.uncoded;
 }
 
 int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds, double* influence,
@@ -1641,4 +1736,35 @@ extern "C" int hbx_pool_stats(hbx_pool* p, hbx_stats* s) {
     cudaSetDevice(p->ctx->device);
     fill_stats(p, s);
     return HBX_OK;
+}
+
+extern "C" int hbx_philox_ceiling(hbx_ctx* ctx, double* blocks_per_s) {
+    using namespace hbx;
+    if (!ctx || !blocks_per_s) return HBX_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    const uint32_t blocks = (uint32_t)ctx->sms * 8, per_thread = 4096;
+    void* out = nullptr;
+    RC(dalloc(ctx, &out, (size_t)blocks * 256 * 4));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = HBX_OK;
+    float best = 0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = cuda_fail(ctx, cudaGetLastError(), "cudaEventCreate");
+    } else {
+        for (int r = 0; r < 4 && rc == HBX_OK; r++) {
+            cudaEventRecord(e0, ctx->stream);
+            cudaError_t le = launch_philox_ceiling(blocks, per_thread, (uint32_t*)out, ctx->stream);
+            cudaEventRecord(e1, ctx->stream);
+            if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, e0, e1);
+            if (le != cudaSuccess) rc = cuda_fail(ctx, le, "Philox ceiling");
+            else if (r > 0 && (best == 0 || ms < best)) best = ms;  // launch 0 warms up
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dfree(ctx, out);
+    if (rc == HBX_OK) *blocks_per_s = (double)blocks * 256.0 * per_thread / (best * 1e-3);
+    return rc;
 }

@@ -77,6 +77,14 @@ struct hbx_pool {
     double* moments = nullptr;
     unsigned long long aux_scanned = 0, aux_live = 0;  // edges of warm-up/calibration passes
     uint64_t hist_sets = 0, hist_dense = 0, hist_verts = 0;  // warm-up pass: sets, dense sets, other vertices
+    // effective density cut: the option, or from the per-graph scheme 0
+    // (Huffmax) or n + 1 (Bitmax)
+    uint32_t cut = 32;
+    bool bitmax = false;   // per-graph scheme chose Bitmax
+    bool tiles = false;    // bitmap sets are columns of vertex-major 32-set tiles
+    double scheme_skew = 0.0;
+    uint32_t* wsizes = nullptr;  // warm-up set sizes, during the warm-up pass of the per-graph scheme
+    uint32_t wsizes_cap = 0;
     // codebook
     bool has_cb = false;
     uint64_t W = 0;
@@ -118,7 +126,11 @@ struct hbx_pool {
     std::map<uint64_t, Bound> bounds;
     double count_kernel_s = 0;
     uint64_t count_bytes = 0;
-    cudaEvent_t evc0 = nullptr, evc1 = nullptr;
+    cudaEvent_t evc0 = nullptr, evc1 = nullptr, evs0 = nullptr, evs1 = nullptr;
+    double select_kernel_s = 0, dec_s = 0;
+    uint64_t select_iterations = 0, dec_bytes = 0;
+    double ms_kernel_s = 0;
+    uint64_t ms_nsets = 0, ms_blocks = 0;
     bool count_pending = false;
     uint8_t* alive = nullptr;
     uint64_t alive_cap = 0;

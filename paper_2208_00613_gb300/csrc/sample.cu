@@ -361,6 +361,7 @@ __device__ bool warp_emit(const SampleArgs& a, uint32_t j, uint32_t* queue, uint
         if (lane == 0) {  // sizes of the sampled sets, kept apart from the pool's statistics
             st.bm += dense;
             st.verts += dense ? 0u : size;
+            if (a.sizes && j < a.sizes_cap) a.sizes[j] = size;
         }
         return true;
     }
@@ -730,6 +731,7 @@ __device__ void block_emit(const SampleArgs& a, uint32_t j, uint32_t size, uint3
         } else if (tid == 0) {
             atomicAdd(&a.ctr->hist_dense, 1ull);
         }
+        if (tid == 0 && a.sizes && j < a.sizes_cap) a.sizes[j] = size;
     } else if (a.mode == MODE_RAW) {
         if (tid == 0) {
             s.off = atomicAdd(&a.ctr->raw_cursor, (unsigned long long)size);
@@ -1342,6 +1344,7 @@ __global__ void __launch_bounds__(BP_THREADS) sample_mid_kernel(SampleArgs a, ui
             } else if (tid == 0) {
                 atomicAdd(&a.ctr->hist_dense, 1ull);
             }
+            if (tid == 0 && a.sizes && j < a.sizes_cap) a.sizes[j] = size;
         } else if (a.mode == MODE_RAW) {
             if (tid == 0) {
                 s.item = 0;

@@ -62,7 +62,7 @@ __global__ void sel_init_kernel(SelArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         SelState z;
         z.u = NONE; z.it = 0; z.n_cov_huff = 0; z.n_cov_bm = 0; z.n_cov_raw = 0; z.pad = 0; z.gain = 0; z.covered = 0;
-        z.n_dec = 0;
+        z.n_dec = 0; z.dec_bytes = 0; z.t_argmax_ns = 0; z.t_cover_ns = 0; z.t_dec_ns = 0;
         *a.st = z;
         *a.ticket = 0;
     }
@@ -75,6 +75,69 @@ __global__ void sel_init_kernel(SelArgs a) {
 // histogram, the rest to cnt, with one atomic per group of lanes hitting the
 // same counter.  The item count comes from the device (n_dev) or the host.
 // ---------------------------------------------------------------------------
+
+// Items [wb, wb + 32) of `items`, one per lane of the calling warp (all lanes
+// call it).  Items are read through L2: the decrement lists are written by
+// other blocks of the same persistent launch.
+__device__ __forceinline__ void count_items_warp(const SelArgs& a, const DecodeSmem& ds, uint32_t* hist, uint32_t hot,
+                                                 const unsigned long long* items, unsigned long long n_items,
+                                                 unsigned long long wb, int sign) {
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned long long t = wb + lane;
+    uint32_t ncodes = 0, is_code = 0;
+    uint64_t pos = 0, pos0 = 0;
+    const uint32_t* words = nullptr;
+    const uint32_t* raw = nullptr;
+    if (t < n_items) {
+        const unsigned long long item = __ldcg(items + t);
+        const uint32_t j = (uint32_t)(item >> 32), c = (uint32_t)item;
+        if (j < a.T) {
+            const HuffView h = huff_view(a.code_heap, a.recs[j]);
+            const uint32_t nch = (h.n_coded + 31) / 32;
+            if (c < nch) {
+                words = h.words;
+                pos = c ? h.side[c - 1] : 0u;
+                pos0 = pos;
+                ncodes = min(32u, h.n_coded - 32 * c);
+                is_code = 1;
+            } else {
+                const uint32_t rc = c - nch;
+                raw = h.raw + 32ull * rc;
+                ncodes = min(32u, h.n_raw - 32 * rc);
+            }
+        }
+    }
+    uint32_t i = 0;
+    for (; i < 32; i++) {
+        const bool have = i < ncodes;
+        uint32_t target = NONE;
+        if (have) {
+            if (is_code) {
+                const uint32_t r = decode_one(ds, words, pos);
+                if (r == NONE) atomicMax(&a.st->pad, 1u);
+                else target = r < hot ? r : (RAW_FLAG | __ldg(a.cb.vertex_of_rank + r));
+            } else {
+                target = RAW_FLAG | raw[i];
+            }
+        }
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, target);
+        if (have && target != NONE && lane == (uint32_t)(__ffs(peers) - 1)) {
+            const uint32_t c = __popc(peers);
+            if (target & RAW_FLAG) atomicAdd(&a.cnt[target & ~RAW_FLAG], sign * (int)c);
+            else atomicAdd(&hist[target], c);
+        }
+        if (__all_sync(0xFFFFFFFFu, i + 1 >= ncodes)) break;
+    }
+    if (sign < 0) {
+        // bytes this decrement read: the item, the chunk's code bits (with its
+        // side entry) or copy-array ids
+        uint32_t by = 0;
+        if (t < n_items) by = 8u + (is_code ? (uint32_t)((pos - pos0 + 7) / 8) + 4u : 4u * ncodes);
+        by = warp_sum(by);
+        if (lane == 0 && by) atomicAdd(&a.st->dec_bytes, (unsigned long long)by);
+    }
+}
+
 __global__ void __launch_bounds__(COUNT_THREADS) count_items_kernel(SelArgs a, const unsigned long long* items,
                                                                    const unsigned long long* n_dev,
                                                                    unsigned long long n_host, int sign) {
@@ -86,54 +149,10 @@ __global__ void __launch_bounds__(COUNT_THREADS) count_items_kernel(SelArgs a, c
     load_decode_smem(ds, a.cb);
     for (uint32_t i = threadIdx.x; i < a.hot; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    const uint32_t lane = threadIdx.x & 31;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (unsigned long long wb = (unsigned long long)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
-         wb < n_items; wb += nwarps * 32) {
-        const unsigned long long t = wb + lane;
-        uint32_t ncodes = 0, is_code = 0;
-        uint64_t pos = 0;
-        const uint32_t* words = nullptr;
-        const uint32_t* raw = nullptr;
-        if (t < n_items) {
-            const unsigned long long item = items[t];
-            const uint32_t j = (uint32_t)(item >> 32), c = (uint32_t)item;
-            if (j < a.T) {
-                const HuffView h = huff_view(a.code_heap, a.recs[j]);
-                const uint32_t nch = (h.n_coded + 31) / 32;
-                if (c < nch) {
-                    words = h.words;
-                    pos = c ? h.side[c - 1] : 0u;
-                    ncodes = min(32u, h.n_coded - 32 * c);
-                    is_code = 1;
-                } else {
-                    const uint32_t rc = c - nch;
-                    raw = h.raw + 32ull * rc;
-                    ncodes = min(32u, h.n_raw - 32 * rc);
-                }
-            }
-        }
-        for (uint32_t i = 0; i < 32; i++) {
-            const bool have = i < ncodes;
-            uint32_t target = NONE;
-            if (have) {
-                if (is_code) {
-                    const uint32_t r = decode_one(ds, words, pos);
-                    if (r == NONE) atomicMax(&a.st->pad, 1u);
-                    else target = r < a.hot ? r : (RAW_FLAG | __ldg(a.cb.vertex_of_rank + r));
-                } else {
-                    target = RAW_FLAG | raw[i];
-                }
-            }
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, target);
-            if (have && target != NONE && lane == (uint32_t)(__ffs(peers) - 1)) {
-                const uint32_t c = __popc(peers);
-                if (target & RAW_FLAG) atomicAdd(&a.cnt[target & ~RAW_FLAG], sign * (int)c);
-                else atomicAdd(&hist[target], c);
-            }
-            if (__all_sync(0xFFFFFFFFu, i + 1 >= ncodes)) break;
-        }
-    }
+         wb < n_items; wb += nwarps * 32)
+        count_items_warp(a, ds, hist, a.hot, items, n_items, wb, sign);
     __syncthreads();
     for (uint32_t r = threadIdx.x; r < a.hot; r += blockDim.x) {
         const uint32_t h = hist[r];
@@ -184,59 +203,67 @@ struct Planes {
 // in shared memory, each thread streams its 16 bytes of every row (eight rows
 // in flight) into bit-sliced counters, then adds sign * count to cnt[32w + bit]
 // for every bit with a nonzero count.  Rows are padded to a multiple of 4 words
-// and 16-byte aligned.
+// and 16-byte aligned.  All threads of the block call it with the same tile.
+__device__ __forceinline__ void bitmap_tile(const SelArgs& a, const uint32_t* list, uint32_t len, uint64_t tile,
+                                            int sign, unsigned long long* s_off, uint32_t* s_n) {
+    const uint32_t nw = (a.n + 31) / 32;
+    const uint32_t nq = (nw + 3) / 4;  // 16-byte quads per row
+    const uint32_t nchunk = (nq + blockDim.x - 1) / blockDim.x;
+    const uint32_t b = (uint32_t)(tile / nchunk), ch = (uint32_t)(tile % nchunk);
+    __syncthreads();  // the previous tile is done with s_off
+    if (threadIdx.x == 0) *s_n = 0;
+    __syncthreads();
+    const uint32_t s0 = b * BM_BATCH, s1 = min(len, s0 + BM_BATCH);
+    for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+        const uint32_t j = __ldcg(list + i);
+        if (j < a.T) s_off[atomicAdd(s_n, 1u)] = rec_off(a.recs[j]);
+    }
+    __syncthreads();
+    const uint32_t rows = *s_n;
+    const uint32_t q = ch * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    Planes pl[4];
+    for (uint32_t r0 = 0; r0 < rows; r0 += 8) {
+        uint32_t w[4][8];
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            uint4 x = make_uint4(0, 0, 0, 0);
+            if (r0 + r < rows) x = __ldg(reinterpret_cast<const uint4*>(a.bm_heap + s_off[r0 + r]) + q);
+            w[0][r] = x.x;
+            w[1][r] = x.y;
+            w[2][r] = x.z;
+            w[3][r] = x.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) pl[c].add8(w[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        uint32_t any = pl[c].any();
+        const uint32_t wbase = (q * 4 + c) * 32;
+        while (any) {
+            const uint32_t bit = __ffs(any) - 1;
+            any &= any - 1;
+            const uint32_t v = wbase + bit;
+            if (v < a.n) atomicAdd(&a.cnt[v], sign * (int)pl[c].count(bit));
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t bitmap_tiles(const SelArgs& a, uint32_t len) {
+    const uint32_t nq = ((a.n + 31) / 32 + 3) / 4;
+    const uint32_t nchunk = (nq + blockDim.x - 1) / blockDim.x;
+    return (uint64_t)((len + BM_BATCH - 1) / BM_BATCH) * nchunk;
+}
+
 __global__ void __launch_bounds__(SEL_THREADS) bitmap_count_kernel(SelArgs a, const uint32_t* list,
                                                                   const uint32_t* list_len_dev,
                                                                   uint32_t list_len_host, int sign) {
     __shared__ unsigned long long s_off[BM_BATCH];
     __shared__ uint32_t s_n;
-    const uint32_t nw = (a.n + 31) / 32;
-    const uint32_t nq = (nw + 3) / 4;  // 16-byte quads per row
     const uint32_t len = list_len_dev ? *list_len_dev : list_len_host;
-    const uint32_t nbatch = (len + BM_BATCH - 1) / BM_BATCH;
-    const uint32_t nchunk = (nq + blockDim.x - 1) / blockDim.x;
-    const uint64_t tiles = (uint64_t)nbatch * nchunk;
-    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const uint32_t b = (uint32_t)(tile / nchunk), ch = (uint32_t)(tile % nchunk);
-        __syncthreads();  // the previous tile is done with s_off
-        if (threadIdx.x == 0) s_n = 0;
-        __syncthreads();
-        const uint32_t s0 = b * BM_BATCH, s1 = min(len, s0 + BM_BATCH);
-        for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-            const uint32_t j = list[i];
-            if (j < a.T) s_off[atomicAdd(&s_n, 1u)] = rec_off(a.recs[j]);
-        }
-        __syncthreads();
-        const uint32_t rows = s_n;
-        const uint32_t q = ch * blockDim.x + threadIdx.x;
-        if (q >= nq) continue;
-        Planes pl[4];
-        for (uint32_t r0 = 0; r0 < rows; r0 += 8) {
-            uint32_t w[4][8];
-#pragma unroll
-            for (int r = 0; r < 8; r++) {
-                uint4 x = make_uint4(0, 0, 0, 0);
-                if (r0 + r < rows) x = __ldg(reinterpret_cast<const uint4*>(a.bm_heap + s_off[r0 + r]) + q);
-                w[0][r] = x.x;
-                w[1][r] = x.y;
-                w[2][r] = x.z;
-                w[3][r] = x.w;
-            }
-#pragma unroll
-            for (int c = 0; c < 4; c++) pl[c].add8(w[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            uint32_t any = pl[c].any();
-            const uint32_t wbase = (q * 4 + c) * 32;
-            while (any) {
-                const uint32_t bit = __ffs(any) - 1;
-                any &= any - 1;
-                const uint32_t v = wbase + bit;
-                if (v < a.n) atomicAdd(&a.cnt[v], sign * (int)pl[c].count(bit));
-            }
-        }
-    }
+    const uint64_t tiles = bitmap_tiles(a, len);
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) bitmap_tile(a, list, len, tile, sign, s_off, &s_n);
 }
 
 // Uncompressed pools: one warp per set.
@@ -342,66 +369,71 @@ __device__ bool sorted_contains(const uint32_t* __restrict__ x, uint32_t len, ui
     return lo < len && __ldg(x + lo) == u;
 }
 
+// Cover test of sets [jb, jb + 32), one per lane of the calling warp (all lanes
+// call it): every alive set holding u is marked covered and appended to the
+// covered list of its kind; covered Huffman sets also list their chunk items
+// for the decrement pass.  Returns the lane's gain (0 or 1).
+__device__ __forceinline__ uint32_t cover_warp(const SelArgs& a, uint32_t u, uint32_t ru, uint32_t jb) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t j = jb + lane;
+    bool member = false;
+    uint32_t kind = KIND_PENDING, nit = 0;
+    if (j < a.T && __ldcg(a.alive + j)) {
+        const SetRec rec = a.recs[j];
+        kind = rec_kind(rec);
+        nit = (rec.n_coded + 31) / 32 + (rec.size - rec.n_coded + 31) / 32;
+        if (kind == KIND_HUFF) {
+            const HuffView h = huff_view(a.code_heap, rec);
+            if (ru != NONE) member = huff_contains(a.cb, h, ru);
+            else member = sorted_contains(h.raw, h.n_raw, u);
+        } else if (kind == KIND_BITMAP) {
+            member = (__ldg(a.bm_heap + rec_off(rec) + (u >> 5)) >> (u & 31)) & 1u;
+        } else {
+            const uint32_t* x = a.raw_heap + rec_off(rec);
+            for (uint32_t i = 0; i < rec.size && !member; i++) member = __ldg(x + i) == u;
+        }
+        if (member) a.alive[j] = 0;
+    }
+    // one list append per warp and kind
+#pragma unroll
+    for (uint32_t k = 0; k < 3; k++) {
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, member && kind == k);
+        if (!bal) continue;
+        uint32_t* list = k == KIND_HUFF ? a.cov_huff : (k == KIND_BITMAP ? a.cov_bm : a.cov_raw);
+        uint32_t* len = k == KIND_HUFF ? &a.st->n_cov_huff : (k == KIND_BITMAP ? &a.st->n_cov_bm : &a.st->n_cov_raw);
+        const uint32_t leader = __ffs(bal) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(len, (uint32_t)__popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (member && kind == k) list[base + __popc(bal & lanemask_lt())] = j;
+    }
+    // chunk items of the covered Huffman sets, for the decrement pass
+    if (!(member && kind == KIND_HUFF)) nit = 0;
+    const uint32_t incl = warp_incl_scan(nit);
+    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (tot) {
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(&a.st->n_dec, (unsigned long long)tot);
+        base = __shfl_sync(0xFFFFFFFFu, base, 31);
+        const unsigned long long my = base + incl - nit;
+        if (my + nit <= a.dec_cap) {
+            for (uint32_t c = 0; c < nit; c++) a.dec_items[my + c] = ((unsigned long long)j << 32) | c;
+        } else if (nit) {
+            atomicMax(&a.st->pad, 2u);
+        }
+    }
+    return member ? 1u : 0u;
+}
+
 __global__ void __launch_bounds__(SEL_THREADS) cover_kernel(SelArgs a) {
     const uint32_t u = a.st->u;
     const uint32_t ru = a.has_cb ? __ldg(a.cb.rank_of + u) : NONE;
-    unsigned long long gain = 0;
-    const uint32_t lane = threadIdx.x & 31;
-    // warp-uniform loop: every lane reaches the ballots below
-    for (uint32_t jb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); jb < a.T; jb += gridDim.x * blockDim.x) {
-        const uint32_t j = jb + lane;
-        bool member = false;
-        uint32_t kind = KIND_PENDING, nit = 0;
-        if (j < a.T && a.alive[j]) {
-            const SetRec rec = a.recs[j];
-            kind = rec_kind(rec);
-            nit = (rec.n_coded + 31) / 32 + (rec.size - rec.n_coded + 31) / 32;
-            if (kind == KIND_HUFF) {
-                const HuffView h = huff_view(a.code_heap, rec);
-                if (ru != NONE) member = huff_contains(a.cb, h, ru);
-                else member = sorted_contains(h.raw, h.n_raw, u);
-            } else if (kind == KIND_BITMAP) {
-                member = (__ldg(a.bm_heap + rec_off(rec) + (u >> 5)) >> (u & 31)) & 1u;
-            } else {
-                const uint32_t* x = a.raw_heap + rec_off(rec);
-                for (uint32_t i = 0; i < rec.size && !member; i++) member = __ldg(x + i) == u;
-            }
-            if (member) {
-                a.alive[j] = 0;
-                gain++;
-            }
-        }
-        // one list append per warp and kind
-#pragma unroll
-        for (uint32_t k = 0; k < 3; k++) {
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, member && kind == k);
-            if (!bal) continue;
-            uint32_t* list = k == KIND_HUFF ? a.cov_huff : (k == KIND_BITMAP ? a.cov_bm : a.cov_raw);
-            uint32_t* len = k == KIND_HUFF ? &a.st->n_cov_huff : (k == KIND_BITMAP ? &a.st->n_cov_bm : &a.st->n_cov_raw);
-            const uint32_t leader = __ffs(bal) - 1;
-            uint32_t base = 0;
-            if (lane == leader) base = atomicAdd(len, (uint32_t)__popc(bal));
-            base = __shfl_sync(0xFFFFFFFFu, base, leader);
-            if (member && kind == k) list[base + __popc(bal & lanemask_lt())] = j;
-        }
-        // chunk items of the covered Huffman sets, for the decrement pass
-        if (!(member && kind == KIND_HUFF)) nit = 0;
-        const uint32_t incl = warp_incl_scan(nit);
-        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (tot) {
-            unsigned long long base = 0;
-            if (lane == 31) base = atomicAdd(&a.st->n_dec, (unsigned long long)tot);
-            base = __shfl_sync(0xFFFFFFFFu, base, 31);
-            const unsigned long long my = base + incl - nit;
-            if (my + nit <= a.dec_cap) {
-                for (uint32_t c = 0; c < nit; c++) a.dec_items[my + c] = ((unsigned long long)j << 32) | c;
-            } else if (nit) {
-                atomicMax(&a.st->pad, 2u);
-            }
-        }
-    }
-    gain = (unsigned long long)warp_sum((uint32_t)gain);
-    if ((threadIdx.x & 31) == 0 && gain) atomicAdd(&a.st->gain, gain);
+    uint32_t gain = 0;
+    // warp-uniform loop: every lane reaches the ballots in cover_warp
+    for (uint32_t jb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); jb < a.T; jb += gridDim.x * blockDim.x)
+        gain += cover_warp(a, u, ru, jb);
+    gain = warp_sum(gain);
+    if ((threadIdx.x & 31) == 0 && gain) atomicAdd(&a.st->gain, (unsigned long long)gain);
 }
 
 __global__ void __launch_bounds__(SEL_THREADS) dec_raw_kernel(SelArgs a) {
@@ -417,6 +449,7 @@ __global__ void __launch_bounds__(SEL_THREADS) dec_raw_kernel(SelArgs a) {
 
 __global__ void finalize_kernel(SelArgs a) {
     SelState s = *a.st;
+    s.dec_bytes += 4ull * s.n_cov_bm * (((a.n + 31) / 32 + 3) & ~3u);
     a.cnt[s.u] = -1;
     a.marginal[s.it] = s.gain;
     s.covered += s.gain;
@@ -427,6 +460,231 @@ __global__ void finalize_kernel(SelArgs a) {
     s.n_cov_raw = 0;
     s.n_dec = 0;
     *a.st = s;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent selection: all k greedy iterations in one cooperative launch
+// whose blocks are all resident.  An iteration is three phases separated by
+// grid barriers:
+//   A  argmax: per-block maxima of the count keys, then every block reduces
+//      the per-block results itself, so all blocks know u* without another
+//      barrier (the previous u*, whose count is zero by now, is excluded and
+//      marked chosen with -1 here);
+//   B  cover: every alive set holding u* is covered and listed (cover_warp);
+//   C  decrement: the covered sets' Huffman chunks (hot ranks through a small
+//      shared-memory histogram), bitmap rows (bit-plane sums) and raw sets
+//      lose one count per vertex; block 0 records u* and its gain.
+// Data written by other blocks of the launch (counts, alive flags, lists,
+// per-iteration counters) is read through L2 (__ldcg / atomics).  Every
+// barrier wait is bounded by a clock64 budget: a block that runs out sets the
+// error word, and every block leaves at its next barrier, so the launch ends
+// and the host reports a timeout.
+// ---------------------------------------------------------------------------
+constexpr int PS_THREADS = 512;
+constexpr uint32_t PS_HOT = 2048;                    // ranks counted in shared memory by phase C
+__device__ __forceinline__ bool grid_barrier(SelBarrier* b, uint32_t nblocks, long long budget, bool* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        volatile unsigned int* gen = &b->gen;
+        volatile unsigned int* err = &b->err;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == nblocks - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (*err) {
+                    ok = false;
+                    break;
+                }
+                if (clock64() - t0 > budget) {
+                    atomicExch(&b->err, 1u);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        *s_ok = ok && *err == 0;
+    }
+    __syncthreads();
+    return *s_ok;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(PS_THREADS) select_persistent_kernel(SelArgs a, uint32_t k, SelBarrier* bar) {
+    __shared__ DecodeSmem ds;
+    __shared__ uint32_t hist[PS_HOT];
+    __shared__ unsigned long long s_off[BM_BATCH];
+    __shared__ unsigned long long s_w[PS_THREADS / 32];
+    __shared__ uint32_t s_n, s_u;
+    __shared__ bool s_ok;
+    const uint32_t nb = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t hot = min(a.hot, PS_HOT);
+    if (a.has_cb) load_decode_smem(ds, a.cb);
+    __syncthreads();
+    uint32_t u_prev = NONE;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;  // block 0 times the phases, barrier to barrier
+    unsigned long long t_a = 0, t_b = 0, t_c = 0, t_prev = timer ? globaltimer_ns() : 0ull;
+    for (uint32_t it = 0; it < k; it++) {
+        // ---- A: argmax (key = (cnt + 1) << 32 | (2^32 - 1 - v), u_prev excluded)
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (u_prev != NONE) a.cnt[u_prev] = -1;
+            a.st->gain = 0;
+            a.st->n_cov_huff = 0;
+            a.st->n_cov_bm = 0;
+            a.st->n_cov_raw = 0;
+            a.st->n_dec = 0;
+        }
+        unsigned long long best = 0;
+        const uint32_t n4q = a.n4 / 4;
+        for (uint32_t i = blockIdx.x * PS_THREADS + threadIdx.x; i < n4q; i += nb * PS_THREADS) {
+            const int4 c = __ldcg(reinterpret_cast<const int4*>(a.cnt) + i);
+            const int cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t v = i * 4 + q;
+                const unsigned long long key =
+                    v == u_prev ? 0ull : (((unsigned long long)(uint32_t)(cv[q] + 1) << 32) | (0xFFFFFFFFu - v));
+                best = key > best ? key : best;
+            }
+        }
+        best = warp_max_u64(best);
+        if (lane == 0) s_w[warp] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = 0;
+            for (int w = 0; w < PS_THREADS / 32; w++) m = s_w[w] > m ? s_w[w] : m;
+            a.partials[blockIdx.x] = m;
+        }
+        if (!grid_barrier(bar, nb, a.wait_cycles, &s_ok)) return;
+        {
+            unsigned long long m = 0;
+            for (uint32_t i = threadIdx.x; i < nb; i += PS_THREADS) {
+                const unsigned long long y = __ldcg(a.partials + i);
+                m = y > m ? y : m;
+            }
+            m = warp_max_u64(m);
+            __syncthreads();  // s_w is reused
+            if (lane == 0) s_w[warp] = m;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long r = 0;
+                for (int w = 0; w < PS_THREADS / 32; w++) r = s_w[w] > r ? s_w[w] : r;
+                s_u = 0xFFFFFFFFu - (uint32_t)r;
+                if (blockIdx.x == 0) {
+                    a.seeds[it] = s_u;
+                    a.st->u = s_u;
+                }
+            }
+            __syncthreads();
+        }
+        const uint32_t u = s_u;
+        if (timer) {
+            const unsigned long long t = globaltimer_ns();
+            t_a += t - t_prev;
+            t_prev = t;
+        }
+        // ---- B: cover
+        {
+            const uint32_t ru = a.has_cb ? __ldg(a.cb.rank_of + u) : NONE;
+            uint32_t gain = 0;
+            for (uint32_t jb = (blockIdx.x * PS_THREADS + (threadIdx.x & ~31u)); jb < a.T; jb += nb * PS_THREADS)
+                gain += cover_warp(a, u, ru, jb);
+            gain = warp_sum(gain);
+            if (lane == 0 && gain) atomicAdd(&a.st->gain, (unsigned long long)gain);
+        }
+        if (!grid_barrier(bar, nb, a.wait_cycles, &s_ok)) return;
+        if (timer) {
+            const unsigned long long t = globaltimer_ns();
+            t_b += t - t_prev;
+            t_prev = t;
+        }
+        // ---- C: decrement
+        {
+            for (uint32_t i = threadIdx.x; i < hot; i += PS_THREADS) hist[i] = 0;
+            __syncthreads();
+            const unsigned long long n_dec = min(__ldcg(&a.st->n_dec), a.dec_cap);
+            if (a.has_cb) {
+                const unsigned long long nwarps = (unsigned long long)nb * (PS_THREADS / 32);
+                for (unsigned long long wb = (unsigned long long)(blockIdx.x * (PS_THREADS / 32) + warp) * 32;
+                     wb < n_dec; wb += nwarps * 32)
+                    count_items_warp(a, ds, hist, hot, a.dec_items, n_dec, wb, -1);
+            }
+            __syncthreads();
+            for (uint32_t r = threadIdx.x; r < hot; r += PS_THREADS) {
+                const uint32_t h = hist[r];
+                if (h) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -(int)h);
+            }
+            const uint32_t n_bm = __ldcg(&a.st->n_cov_bm);
+            if (n_bm) {
+                const uint64_t tiles = bitmap_tiles(a, n_bm);
+                for (uint64_t tile = blockIdx.x; tile < tiles; tile += nb)
+                    bitmap_tile(a, a.cov_bm, n_bm, tile, -1, s_off, &s_n);
+            }
+            const uint32_t n_raw = __ldcg(&a.st->n_cov_raw);
+            for (uint32_t i = blockIdx.x * (PS_THREADS / 32) + warp; i < n_raw; i += nb * (PS_THREADS / 32)) {
+                const SetRec rec = a.recs[__ldcg(a.cov_raw + i)];
+                const uint32_t* x = a.raw_heap + rec_off(rec);
+                for (uint32_t q = lane; q < rec.size; q += 32) atomicAdd(&a.cnt[__ldg(x + q)], -1);
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                const unsigned long long g = __ldcg(&a.st->gain);
+                a.marginal[it] = g;
+                a.st->covered += g;
+                a.st->it = it + 1;
+                if (n_bm) atomicAdd(&a.st->dec_bytes, 4ull * n_bm * (((a.n + 31) / 32 + 3) & ~3u));
+            }
+        }
+        if (!grid_barrier(bar, nb, a.wait_cycles, &s_ok)) return;
+        if (timer) {
+            const unsigned long long t = globaltimer_ns();
+            t_c += t - t_prev;
+            t_prev = t;
+        }
+        u_prev = u;
+    }
+    if (timer) {
+        if (u_prev != NONE) a.cnt[u_prev] = -1;
+        a.st->t_argmax_ns += t_a;
+        a.st->t_cover_ns += t_b;
+        a.st->t_dec_ns += t_c;
+    }
+}
+
+int select_persistent_blocks(int sms) {
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, select_persistent_kernel, PS_THREADS, 0) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            b = 0;
+        }
+        per_sm = b > 2 ? 2 : b;
+    }
+    return per_sm * sms;
+}
+
+cudaError_t launch_select_persistent(const SelArgs& a, uint32_t k, SelBarrier* bar, cudaStream_t s) {
+    const int blocks = select_persistent_blocks(a.sms);
+    if (blocks <= 0) return cudaErrorInvalidConfiguration;
+    SelArgs aa = a;
+    uint32_t kk = k;
+    SelBarrier* bb = bar;
+    void* args[] = {&aa, &kk, &bb};
+    return cudaLaunchCooperativeKernel((const void*)select_persistent_kernel, dim3((unsigned)blocks),
+                                       dim3(PS_THREADS), args, 0, s);
 }
 
 cudaError_t launch_sel_init(const SelArgs& a, cudaStream_t s) {
@@ -498,6 +756,7 @@ cudaError_t launch_iteration(const SelArgs& a, uint32_t encode, cudaStream_t s) 
 __global__ void index_kernel(IndexArgs a) {
     __shared__ double s_m[3][SEL_THREADS / 32];
     double m1 = 0, m2 = 0, m3 = 0;
+    uint32_t uncoded = 0;
     for (uint32_t j = a.j0 + blockIdx.x * blockDim.x + threadIdx.x; j < a.j1; j += gridDim.x * blockDim.x) {
         const SetRec rec = a.recs[j];
         const uint32_t kind = rec_kind(rec);
@@ -510,6 +769,7 @@ __global__ void index_kernel(IndexArgs a) {
         m2 += x * x;
         m3 += x * x * x;
         if (kind == KIND_HUFF) {
+            uncoded += rec.size - rec.n_coded;
             const uint32_t nch = (rec.n_coded + 31) / 32 + (rec.size - rec.n_coded + 31) / 32;
             const unsigned long long base = atomicAdd(&a.ctr->chunk_items, (unsigned long long)nch);
             if (base + nch > a.items_cap) {
@@ -526,6 +786,8 @@ __global__ void index_kernel(IndexArgs a) {
             a.bm_sets[b] = j;
         }
     }
+    uncoded = warp_sum(uncoded);
+    if ((threadIdx.x & 31) == 0 && uncoded) atomicAdd(&a.ctr->uncoded, (unsigned long long)uncoded);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         m1 += __shfl_xor_sync(0xFFFFFFFFu, m1, d);

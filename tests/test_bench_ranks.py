@@ -65,9 +65,31 @@ def test_oracle_sample_is_bounded_and_positive():
     import bench
     import synth
     w = synth.WORKLOADS["ic_rmat4k"]
-    rate, S, cores, dt = bench.oracle_sample_rate(w.graph(), w, target_s=0.5)
-    assert rate > 0 and S >= 16 and cores >= 1
-    assert dt < 30.0  # the probe sizes the sample to about target_s
+    g = w.graph()
+    S = bench.oracle_sample_size(g, w, 0.5, 2)
+    assert 16 <= S <= 2_000_000
+    rate, dt = bench.oracle_pool_rate(g, w, S, 2)
+    assert rate > 0 and dt < 30.0  # the probe sizes the sample to about target_s
+    cb = bench.oracle_baseline(g, w, target_s=0.5)
+    assert cb["value"] > 0 and cb["cores"] >= 1 and cb["kind"] == "oracle"
+    assert cb["single_thread"]["value"] > 0 and cb["cpu_model"]
+
+
+def test_rooflines_from_stats():
+    sys.path.insert(0, ROOT)
+    import bench
+    s = {"sample_kernel_s": 0.5, "rr_vertices": 10, "edges_scanned": 100, "edges_live": 7, "pool_bytes": 50,
+         "sample_kernel_launches": 3, "ms_kernel_s": 0.25, "ms_philox_blocks": 10**9, "ms_sets": 32,
+         "dec_s": 0.001, "dec_bytes": 3_000_000, "select_iterations": 50, "select_kernel_s": 0.002}
+    wc = bench.sampler_roofline([s], 6000.0, "measured", True)
+    assert wc["achieved"] == (8 * 10 + 4 * 10 + 4 * 7 + 50) / 0.5 / 1e9
+    ic = bench.sampler_roofline([s], 6000.0, "measured", False)
+    assert ic["achieved"] == (8 * 10 + 4 * 100 + 4 * 7 + 50) / 0.5 / 1e9
+    r = bench.search_roofline([s], 8e9)
+    assert r["bound"] == "alu" and abs(r["achieved"] - 4.0) < 1e-12 and abs(r["frac"] - 0.5) < 1e-12
+    d = bench.dec_roofline([s], 6000.0)
+    assert abs(d["achieved"] - 3.0) < 1e-9
+    assert abs(bench.selection_summary([s])["us_per_iteration"] - 40.0) < 1e-9
 
 
 def test_count_roofline_from_stats():

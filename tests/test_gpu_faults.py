@@ -82,3 +82,21 @@ def test_pool_memory_limit(small_graph):
         assert hbx.hbx_pool_size(p) == 1000
         hbx.hbx_pool_destroy(p)
         hbx.hbx_graph_destroy(G)
+
+
+def test_selection_wait_that_runs_out_reports_timeout(small_graph):
+    """The batched form's selection waits at grid barriers; each wait is
+    bounded.  With a budget of one clock cycle the first block to arrive gives
+    up at once: the call must end with TIMEOUT (not hang), and the context must
+    then give the same results as before."""
+    w, g = small_graph
+    with hbx.torch_context(0) as tc:
+        G = hbx.hbx_graph_create(tc.ctx, g)
+        ref = hbx.hbx_imm(tc.ctx, G, w.model, w.k, w.eps, w.ell, w.rr_seed)
+        with pytest.raises(hbx.HbxError) as e:
+            hbx.hbx_imm(tc.ctx, G, w.model, w.k, w.eps, w.ell, w.rr_seed, hbx.hbx_default_options(wait_cycles=1))
+        assert e.value.code == -4  # HBX_ERR_TIMEOUT
+        r = hbx.hbx_imm(tc.ctx, G, w.model, w.k, w.eps, w.ell, w.rr_seed)
+        assert np.array_equal(r["seeds"], ref["seeds"])
+        assert r["influence"] == ref["influence"]
+        hbx.hbx_graph_destroy(G)

@@ -186,7 +186,9 @@ def test_giant_ic_sets_bit_parallel(ctx, cut):
     _check_encoded(ctx, p, op, g, W, cut, T, sample=range(0, T, 5))
     st = hbx.hbx_pool_stats(ctx, p)
     sc, lv = op.edge_counts()
-    assert st["edges_scanned"] == sc and st["edges_live"] == lv
+    # the bit-parallel search skips the coins of edges into sources a set has
+    # already visited: scanned edges are exact, live edges a subset
+    assert st["edges_scanned"] == sc and 0 < st["edges_live"] <= lv
     assert st["rr_vertices"] == int(sizes.sum())
     assert st["sets_bitmap"] == int((cut * sizes > g.n).sum())
     if cut == 2:
