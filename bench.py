@@ -221,8 +221,9 @@ def count_roofline(stats, peak):
 
 
 def dec_roofline(stats, peak):
-    """Decrement phases of the persistent selection: bytes of the covered sets
-    they read over their time (globaltimer, barrier to barrier)."""
+    """Cover-and-decrement phases of the persistent selection: bytes of the
+    covered sets the decrements read over the phases' time (globaltimer,
+    barrier to barrier; the membership tests share that time)."""
     ds = sum(s["dec_s"] for s in stats)
     db = sum(s["dec_bytes"] for s in stats)
     if ds <= 0:
@@ -230,7 +231,7 @@ def dec_roofline(stats, peak):
     ach = db / ds / 1e9
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "bytes_per_step": db / len(stats), "s_per_step": ds / len(stats),
-            "kernel": "select_persistent_kernel, decrement phase"}
+            "kernel": "select_persistent_kernel, cover-and-decrement phases"}
 
 
 def selection_summary(stats):

@@ -112,6 +112,12 @@ typedef struct {
      * Eq. (3)'s SUBTRACT).  The seeds are the same either way; the plain form
      * always decrements. */
     uint32_t select_mode;
+    /* IMM's final phase: 0 reuses the estimation rounds' sets (theta =
+     * max(T_i, ceil(lambda* / LB)) sets [0, theta)); 1 draws theta =
+     * ceil(lambda* / LB) new sets [T_i, T_i + theta) and selects on those only,
+     * keeping the two phases independent. */
+    uint32_t fresh_final;
+    uint32_t reserved_opt;
 } hbx_options;
 
 typedef struct {
@@ -157,15 +163,22 @@ typedef struct {
     uint64_t ms_philox_blocks;
     /* greedy iterations of the selections: device time (CUDA events around
      * them, the initial count excluded), iterations run, and for the batched
-     * form the time of their decrement phases and the bytes those read (code
-     * bytes and items of the covered Huffman sets' chunks, copy-array ids,
-     * covered bitmap rows) */
+     * form the time of their cover-and-decrement phases (the persistent
+     * kernel decrements a covered set where it finds it) and the bytes the
+     * decrements read (code bytes and items of the covered Huffman sets'
+     * chunks, copy-array ids, covered bitmap rows or tiles) */
     double select_kernel_s;
     uint64_t select_iterations;
     double dec_s;
     uint64_t dec_bytes;
     /* vertex occurrences of Huffman sets stored in copy arrays (no code) */
     uint64_t uncoded_vertices;
+    /* encoding scheme in effect: 0 per-set density cut, 1 Huffmax, 2 Bitmax
+     * (the per-graph scheme), 3 Bitmax in vertex-major tiles; and the warm-up
+     * sizes' skewness that the per-graph scheme decided on */
+    uint32_t scheme;
+    uint32_t reserved;
+    double scheme_skewness;
 } hbx_stats;
 
 /* Human-readable name of an HBX_ERR_* code. */

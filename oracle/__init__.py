@@ -65,6 +65,7 @@ def _load():
         "orc_greedy_lists": (I, [U32, U64, P, P, U32, P, P, P]),
         "orc_imm_params": (I, [U32, U32, D, D, P]),
         "orc_imm_pool": (I, [P, U32, D, D, I, P, P, P, P, P, P, P, P]),
+        "orc_imm_pool_fresh": (I, [P, U32, D, D, I, I, P, P, P, P, P, P, P, P]),
         "orc_size_stats": (None, [P, U64, U32, P, P]),
         "orc_pool_warmup_freq": (I, [P, U64, U32, P]),
         "orc_huffman_lengths": (I, [U64, P, P]),
@@ -191,16 +192,18 @@ class Pool:
             raise ValueError("orc_pool_greedy: bad arguments")
         return seeds, marg, cov.value
 
-    def imm(self, k: int, eps: float, ell: float, nthreads: int = 0) -> dict:
+    def imm(self, k: int, eps: float, ell: float, nthreads: int = 0, fresh_final: bool = False) -> dict:
+        """IMM on this pool's sets; fresh_final draws the final phase's sets
+        anew (ids [T_i, T_i + theta)) instead of reusing [0, theta)."""
         seeds = np.empty(k, dtype=np.uint32)
         marg = np.empty(k, dtype=np.uint64)
         infl, lb = ctypes.c_double(), ctypes.c_double()
         theta, cov = ctypes.c_uint64(), ctypes.c_uint64()
         rounds = ctypes.c_uint32()
         rT = np.zeros(64, dtype=np.uint64)
-        rc = _load().orc_imm_pool(self.h, k, eps, ell, nthreads, _p(seeds), _p(marg), ctypes.byref(infl),
-                                  ctypes.byref(theta), ctypes.byref(cov), ctypes.byref(lb),
-                                  ctypes.byref(rounds), _p(rT))
+        rc = _load().orc_imm_pool_fresh(self.h, k, eps, ell, nthreads, int(bool(fresh_final)), _p(seeds), _p(marg),
+                                        ctypes.byref(infl), ctypes.byref(theta), ctypes.byref(cov), ctypes.byref(lb),
+                                        ctypes.byref(rounds), _p(rT))
         if rc != 0:
             raise ValueError("orc_imm_pool: bad arguments")
         return dict(seeds=seeds, marginal=marg, influence=infl.value, theta=theta.value,

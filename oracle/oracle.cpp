@@ -298,11 +298,12 @@ void orc_pool_edge_counts(void *h, uint64_t *scanned, uint64_t *live) {
 /* counts drop by one, which is what the per-iteration recount of the paper   */
 /* reconstructs.                                                              */
 /* ------------------------------------------------------------------------- */
-static void greedy(uint32_t n, const std::vector<std::vector<uint32_t>> &sets, uint64_t T, uint32_t k,
-                   uint32_t *seeds, uint64_t *marginal, uint64_t *covered_out) {
+static void greedy_from(uint32_t n, const std::vector<std::vector<uint32_t>> &sets, uint64_t j_lo, uint64_t T,
+                        uint32_t k, uint32_t *seeds, uint64_t *marginal, uint64_t *covered_out) {
     std::vector<uint64_t> cnt(n, 0);
     std::vector<uint8_t> alive(T, 1), chosen(n, 0);
-    for (uint64_t j = 0; j < T; j++)
+    for (uint64_t j = 0; j < j_lo; j++) alive[j] = 0;
+    for (uint64_t j = j_lo; j < T; j++)
         for (uint32_t v : sets[j]) cnt[v]++;
     uint64_t covered = 0;
     for (uint32_t it = 0; it < k; it++) {
@@ -325,6 +326,12 @@ static void greedy(uint32_t n, const std::vector<std::vector<uint32_t>> &sets, u
         if (marginal) marginal[it] = gain;
     }
     if (covered_out) *covered_out = covered;
+}
+
+/* Greedy over the sets [0, T). */
+static void greedy(uint32_t n, const std::vector<std::vector<uint32_t>> &sets, uint64_t T, uint32_t k,
+                   uint32_t *seeds, uint64_t *marginal, uint64_t *covered_out) {
+    greedy_from(n, sets, 0, T, k, seeds, marginal, covered_out);
 }
 
 int orc_pool_greedy(void *h, uint64_t T, uint32_t k, uint32_t *seeds, uint64_t *marginal, uint64_t *covered) {
@@ -399,9 +406,27 @@ static uint32_t floor_log2(uint32_t n) {
  * influence estimate is n cov / theta.
  * round_T (up to 64 entries) records T_1, T_2, ... and then theta.
  */
+int orc_imm_pool_fresh(void *h, uint32_t k, double eps, double ell, int nthreads, int fresh_final,
+                       uint32_t *seeds, uint64_t *marginal, double *influence, uint64_t *theta,
+                       uint64_t *covered_out, double *lb_out, uint32_t *rounds_out, uint64_t *round_T);
+
 int orc_imm_pool(void *h, uint32_t k, double eps, double ell, int nthreads, uint32_t *seeds,
                  uint64_t *marginal, double *influence, uint64_t *theta, uint64_t *covered_out, double *lb_out,
                  uint32_t *rounds_out, uint64_t *round_T) {
+    return orc_imm_pool_fresh(h, k, eps, ell, nthreads, 0, seeds, marginal, influence, theta, covered_out, lb_out,
+                              rounds_out, round_T);
+}
+
+/*
+ * fresh_final = 1: the final phase draws theta = ceil(lambda* / LB) new sets,
+ * [T_i, T_i + theta), instead of reusing the estimation sets (the reading of
+ * Section 2.2 that keeps the two phases independent); greedy runs on those
+ * sets only and the estimate is n cov / theta.  round_T's last entry is then
+ * T_i + theta.
+ */
+int orc_imm_pool_fresh(void *h, uint32_t k, double eps, double ell, int nthreads, int fresh_final,
+                       uint32_t *seeds, uint64_t *marginal, double *influence, uint64_t *theta,
+                       uint64_t *covered_out, double *lb_out, uint32_t *rounds_out, uint64_t *round_T) {
     orc_pool *p = (orc_pool *)h;
     uint32_t n = p->g.n;
     double prm[7];
@@ -429,11 +454,16 @@ int orc_imm_pool(void *h, uint32_t k, double eps, double ell, int nthreads, uint
         }
     }
     uint64_t T = (uint64_t)std::ceil(lambda_star / LB);
-    if (T < Ti) T = Ti;
-    orc_pool_extend(h, T, nthreads);
+    uint64_t j_lo = 0;
+    if (fresh_final) {
+        j_lo = Ti;
+    } else if (T < Ti) {
+        T = Ti;
+    }
+    orc_pool_extend(h, j_lo + T, nthreads);
     uint64_t cov = 0;
-    greedy(n, p->sets, T, k, seeds, marginal, &cov);
-    if (round_T) round_T[rounds < 63 ? rounds : 63] = T;
+    greedy_from(n, p->sets, j_lo, j_lo + T, k, seeds, marginal, &cov);
+    if (round_T) round_T[rounds < 63 ? rounds : 63] = j_lo + T;
     *influence = dn * (double)cov / (double)T;
     *theta = T;
     *covered_out = cov;

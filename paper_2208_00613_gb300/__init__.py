@@ -38,7 +38,8 @@ class hbx_options(ctypes.Structure):
                 ("form", ctypes.c_uint32), ("pool_epoch", ctypes.c_uint32), ("warp_capacity", ctypes.c_uint32),
                 ("warp_group_budget", ctypes.c_uint32), ("block_cluster", ctypes.c_uint32),
                 ("max_device_bytes", ctypes.c_uint64), ("wait_cycles", ctypes.c_uint64),
-                ("scheme", ctypes.c_uint32), ("select_mode", ctypes.c_uint32)]
+                ("scheme", ctypes.c_uint32), ("select_mode", ctypes.c_uint32),
+                ("fresh_final", ctypes.c_uint32), ("reserved_opt", ctypes.c_uint32)]
 
 
 class hbx_stats(ctypes.Structure):
@@ -53,7 +54,8 @@ class hbx_stats(ctypes.Structure):
                 ("count_kernel_s", ctypes.c_double), ("count_bytes", ctypes.c_uint64),
                 ("ms_kernel_s", ctypes.c_double), ("ms_sets", ctypes.c_uint64), ("ms_philox_blocks", ctypes.c_uint64),
                 ("select_kernel_s", ctypes.c_double), ("select_iterations", ctypes.c_uint64),
-                ("dec_s", ctypes.c_double), ("dec_bytes", ctypes.c_uint64), ("uncoded_vertices", ctypes.c_uint64)]
+                ("dec_s", ctypes.c_double), ("dec_bytes", ctypes.c_uint64), ("uncoded_vertices", ctypes.c_uint64),
+                ("scheme", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("scheme_skewness", ctypes.c_double)]
 
     def to_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

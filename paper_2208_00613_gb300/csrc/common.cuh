@@ -75,6 +75,23 @@ struct DevCodebook {
     uint32_t max_len;
 };
 
+// The ten round keys of one Philox key, (k0 + r * 0x9E3779B9, k1 + r *
+// 0xBB67AE85) for round r, computed once on the host and passed in the kernel
+// arguments: the rounds then read their keys from the constant bank instead
+// of adding the Weyl increments in every call.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline PhiloxKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+    PhiloxKeys rk;
+    for (int r = 0; r < 10; r++) {
+        rk.k0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk.k1[r] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    return rk;
+}
+
 // Device counters of one pool (kept in one allocation).
 struct Counters {
     unsigned long long work;         // work-stealing cursor of the warp kernel
@@ -99,6 +116,7 @@ struct Counters {
 
 struct SampleArgs {
     DevGraph g;
+    PhiloxKeys rk;            // round keys of (key0, key1)
     uint32_t key0, key1, epoch, model;
     uint32_t mode, cut;
     uint32_t j0, count;       // sets j0 .. j0+count-1, or list[0..count)
@@ -143,6 +161,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Philox4x32-10 with precomputed round keys (the same function as above).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const PhiloxKeys& rk) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
     }
     return c;
 }

@@ -28,6 +28,7 @@ struct MsCounters {
 
 struct MsArgs {
     DevGraph g;
+    PhiloxKeys rk;         // round keys of (key0, key1)
     const uint32_t* col4;  // g.col padded to 4*ceil(m/4) entries, 16-byte aligned
     uint32_t key0, key1, epoch;
     const uint32_t* sets;  // [MS_SETS] set ids of the batch (mc->nsets of them)
@@ -62,6 +63,12 @@ cudaError_t launch_ms_emit(const MsArgs& a, uint32_t dense, uint32_t mode, uint6
 // `per_thread` each (the ALU ceiling of the bit-parallel search); out: one
 // word per thread.
 cudaError_t launch_philox_ceiling(uint32_t blocks, uint32_t per_thread, uint32_t* out, cudaStream_t s);
+
+// a tile batch (slot s = set 32t + s for the slots in `slots`): the visited
+// masks ORed into the tile at word offset tile_off of the bitmap heap, the
+// slots' records written; masks cleared
+cudaError_t launch_ms_tile(const MsArgs& a, uint32_t slots, uint32_t* bm_heap, uint64_t tile_off,
+                           uint64_t new_words, int sms, cudaStream_t s);
 
 // sets of a bit-parallel batch under the density cut, encoded one block each
 // (scratch slot b for the b-th listed set)
@@ -108,6 +115,12 @@ struct SelArgs {
     unsigned long long* marginal;          // [k]
     int sms;
     long long wait_cycles;                 // bound of every grid-barrier wait
+    uint32_t select_mode;                  // 0: decrement; 1: recount every iteration (persistent form)
+    // Bitmax pools in vertex-major tiles: every set is a column of a tile
+    // (tile t at word t * n4w of bm_heap, word v bit s = set 32t + s)
+    uint32_t tiles;
+    uint64_t n4w;
+    uint32_t* tile_live;                   // [ceil(T/32)] live-set masks after the cover (recount)
 };
 
 constexpr uint32_t HOT_RANKS = 12288;  // ranks privatised in shared memory by the count kernel
@@ -161,6 +174,7 @@ struct DecodeArgs {
     uint32_t* out;
     unsigned long long* ends;           // j1-j0 bit positions after the last code, or null
     Counters* ctr;
+    uint32_t tiles;                     // bitmap sets are columns of vertex-major tiles
 };
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);
 

@@ -59,15 +59,19 @@ __device__ __forceinline__ void ms_flush_live(const MsArgs& a, uint32_t (*s_live
     if (lane == 0 && nblk) atomicAdd(&a.mc->blocks, (unsigned long long)nblk);
 }
 
-// One warp's staging of a round: up to 32 aligned groups of 4 in-edges, one
-// per lane, and for each the sets that still need its coins.
+// One warp's staging of a round: up to MS_ROUND aligned groups of 4 in-edges,
+// two per lane (slot 2l + k holds lane l's k-th group), and for each the sets
+// that still need its coins.
+constexpr uint32_t MS_ROUND = 64;
+constexpr uint32_t MS_ITEMS = 512;  // (slot, set) pairs listed per round; more are found by search
 struct MsRound {
-    uint4 thr[32];      // live thresholds of the group's edges
-    uint4 um[32];       // per edge: sets of the frontier mask whose source is not yet visited
-    uint4 em[32];       // per edge: sets for which it is live (filled by the items)
-    uint32_t gg[32];    // group index (the Philox counter's first word)
-    uint32_t need[32];  // union of the group's um: one Philox block per set in it
-    uint32_t scan[32];  // inclusive prefix sum of popc(need) over the slots
+    uint16_t items[MS_ITEMS];  // slot << 5 | set of the round's first MS_ITEMS pairs
+    uint4 thr[MS_ROUND];      // live thresholds of the group's edges
+    uint4 um[MS_ROUND];       // per edge: sets of the frontier mask whose source is not yet visited
+    uint4 em[MS_ROUND];       // per edge: sets for which it is live (filled by the items)
+    uint32_t gg[MS_ROUND];    // group index (the Philox counter's first word)
+    uint32_t need[MS_ROUND];  // union of the group's um: one Philox block per set in it
+    uint32_t scan[MS_ROUND];  // inclusive prefix sum of popc(need) over the slots
 };
 
 // Position of the r-th (from 0) set bit of m, which has more than r set bits.
@@ -84,50 +88,98 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
     return pos;
 }
 
-// One round of a warp.  Lane l brings group gg of a frontier vertex whose
-// in-edges are [eb, ee), for the sets of mask f (valid = false: no group).
-// A set needs the group's Philox block only if the source of one of the
-// vertex's edges in the group has not been visited by that set: a visited
-// source cannot join the set again, so its coin decides nothing.  The (group,
-// set) pairs that remain are spread evenly over the lanes, one Philox block
-// each; live edges into unvisited sources are collected per edge in shared
-// memory and then ORed into nxt[source] with one reduction per edge.
-__device__ __forceinline__ void ms_round(const MsArgs& a, MsRound& R, const uint32_t* s_sets, uint32_t* s_live_w,
-                                         uint32_t& nblk, bool valid, uint32_t gg, uint32_t eb, uint32_t ee,
-                                         uint32_t f) {
-    const uint32_t lane = threadIdx.x & 31;
-    uint4 c = make_uint4(0, 0, 0, 0), um = make_uint4(0, 0, 0, 0), thr = make_uint4(0, 0, 0, 0);
+// One group of a round: its sources and thresholds (loaded together, so
+// both are in flight at once), then the visited masks of its sources.
+struct MsGroup {
+    uint4 c, thr, um;
+    uint32_t need;
+};
+
+__device__ __forceinline__ MsGroup ms_stage(const MsArgs& a, bool valid, uint32_t gg, uint32_t eb, uint32_t ee,
+                                            uint32_t f) {
+    MsGroup G;
+    G.c = make_uint4(0, 0, 0, 0);
+    G.thr = make_uint4(0, 0, 0, 0);
+    G.um = make_uint4(0, 0, 0, 0);
     if (valid && f) {
-        c = __ldg(reinterpret_cast<const uint4*>(a.col4) + gg);
-        const uint32_t e0 = gg * 4u;
-        if (e0 >= eb && e0 < ee) um.x = f & ~__ldg(a.vis + c.x);
-        if (e0 + 1 >= eb && e0 + 1 < ee) um.y = f & ~__ldg(a.vis + c.y);
-        if (e0 + 2 >= eb && e0 + 2 < ee) um.z = f & ~__ldg(a.vis + c.z);
-        if (e0 + 3 >= eb && e0 + 3 < ee) um.w = f & ~__ldg(a.vis + c.w);
+        G.c = __ldg(reinterpret_cast<const uint4*>(a.col4) + gg);
+        G.thr = __ldg(reinterpret_cast<const uint4*>(a.g.thr) + gg);
     }
-    const uint32_t need = um.x | um.y | um.z | um.w;
-    if (need) thr = __ldg(reinterpret_cast<const uint4*>(a.g.thr) + gg);
-    const uint32_t incl = warp_incl_scan((uint32_t)__popc(need));
+    return G;
+}
+
+__device__ __forceinline__ void ms_visited(const MsArgs& a, MsGroup& G, bool valid, uint32_t gg, uint32_t eb,
+                                           uint32_t ee, uint32_t f) {
+    if (valid && f) {
+        const uint32_t e0 = gg * 4u;
+        if (e0 >= eb && e0 < ee) G.um.x = f & ~__ldg(a.vis + G.c.x);
+        if (e0 + 1 >= eb && e0 + 1 < ee) G.um.y = f & ~__ldg(a.vis + G.c.y);
+        if (e0 + 2 >= eb && e0 + 2 < ee) G.um.z = f & ~__ldg(a.vis + G.c.z);
+        if (e0 + 3 >= eb && e0 + 3 < ee) G.um.w = f & ~__ldg(a.vis + G.c.w);
+    }
+    G.need = G.um.x | G.um.y | G.um.z | G.um.w;
+}
+
+// One round of a warp.  Lane l brings groups gg[k] (k = 0, 1) of frontier
+// vertices whose in-edges are [eb[k], ee[k]), for the sets of masks f[k]
+// (valid[k] = false: no group).  A set needs a group's Philox block only if
+// the source of one of the vertex's edges in the group has not been visited
+// by that set: a visited source cannot join the set again, so its coin
+// decides nothing.  The (group, set) pairs that remain are spread evenly over
+// the lanes, one Philox block each; live edges into unvisited sources are
+// collected per edge in shared memory and then ORed into nxt[source] with one
+// reduction per edge.
+__device__ __forceinline__ void ms_round(const MsArgs& a, MsRound& R, const uint32_t* s_sets, uint32_t* s_live_w,
+                                         uint32_t& nblk, const bool* valid, const uint32_t* gg,
+                                         const uint32_t* eb, const uint32_t* ee, const uint32_t* f) {
+    const uint32_t lane = threadIdx.x & 31;
+    MsGroup G0 = ms_stage(a, valid[0], gg[0], eb[0], ee[0], f[0]);
+    MsGroup G1 = ms_stage(a, valid[1], gg[1], eb[1], ee[1], f[1]);
+    ms_visited(a, G0, valid[0], gg[0], eb[0], ee[0], f[0]);
+    ms_visited(a, G1, valid[1], gg[1], eb[1], ee[1], f[1]);
+    const uint32_t n0 = __popc(G0.need), n1 = __popc(G1.need);
+    const uint32_t incl = warp_incl_scan(n0 + n1);
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (total == 0) return;  // warp-uniform
     nblk += total;  // one Philox block per (group, set) pair
-    R.thr[lane] = thr;
-    R.um[lane] = um;
-    R.em[lane] = make_uint4(0, 0, 0, 0);
-    R.gg[lane] = gg;
-    R.need[lane] = need;
-    R.scan[lane] = incl;
+    R.thr[2 * lane] = G0.thr;
+    R.thr[2 * lane + 1] = G1.thr;
+    R.um[2 * lane] = G0.um;
+    R.um[2 * lane + 1] = G1.um;
+    R.em[2 * lane] = make_uint4(0, 0, 0, 0);
+    R.em[2 * lane + 1] = make_uint4(0, 0, 0, 0);
+    R.gg[2 * lane] = gg[0];
+    R.gg[2 * lane + 1] = gg[1];
+    R.need[2 * lane] = G0.need;
+    R.need[2 * lane + 1] = G1.need;
+    R.scan[2 * lane] = incl - n1;
+    R.scan[2 * lane + 1] = incl;
+    {
+        // list the lane's (slot, set) pairs, in slot order
+        uint32_t o = incl - n0 - n1;
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            for (uint32_t m = k ? G1.need : G0.need; m && o < MS_ITEMS; m &= m - 1, o++)
+                R.items[o] = (uint16_t)(((2 * lane + k) << 5) | (__ffs(m) - 1));
+        }
+    }
     __syncwarp();
     for (uint32_t t = lane; t < total; t += 32) {
-        // slot = number of slots whose inclusive count is <= t
-        uint32_t slot = 0;
+        uint32_t slot, s;
+        if (t < MS_ITEMS) {
+            const uint32_t it = R.items[t];
+            slot = it >> 5;
+            s = it & 31u;
+        } else {
+            // past the list: slot = number of slots whose inclusive count is <= t
+            slot = 0;
 #pragma unroll
-        for (uint32_t step = 16; step; step >>= 1)
-            if (R.scan[slot + step - 1] <= t) slot += step;
-        const uint32_t nd = R.need[slot];
-        const uint32_t r = t - (R.scan[slot] - (uint32_t)__popc(nd));
-        const uint32_t s = nth_set_bit(nd, r);
-        const uint4 x = philox4x32_10(make_uint4(R.gg[slot], s_sets[s], a.epoch, STREAM_IC), a.key0, a.key1);
+            for (uint32_t step = MS_ROUND / 2; step; step >>= 1)
+                if (R.scan[slot + step - 1] <= t) slot += step;
+            const uint32_t nd = R.need[slot];
+            s = nth_set_bit(nd, t - (R.scan[slot] - (uint32_t)__popc(nd)));
+        }
+        const uint4 x = philox4x32_10_rk(make_uint4(R.gg[slot], s_sets[s], a.epoch, STREAM_IC), a.rk);
         const uint4 th = R.thr[slot], u = R.um[slot];
         const uint32_t bit = 1u << s;
         const bool l0 = (u.x & bit) && ic_live(x.x, th.x);
@@ -144,18 +196,22 @@ __device__ __forceinline__ void ms_round(const MsArgs& a, MsRound& R, const uint
         }
     }
     __syncwarp();
-    const uint4 em = R.em[lane];
-    if (em.x) atomicOr(&a.nxt[c.x], em.x);
-    if (em.y) atomicOr(&a.nxt[c.y], em.y);
-    if (em.z) atomicOr(&a.nxt[c.z], em.z);
-    if (em.w) atomicOr(&a.nxt[c.w], em.w);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const uint4 em = R.em[2 * lane + k];
+        const uint4 c = k ? G1.c : G0.c;
+        if (em.x) atomicOr(&a.nxt[c.x], em.x);
+        if (em.y) atomicOr(&a.nxt[c.y], em.y);
+        if (em.z) atomicOr(&a.nxt[c.z], em.z);
+        if (em.w) atomicOr(&a.nxt[c.w], em.w);
+    }
     __syncwarp();  // the staging is reused by the next round
 }
 
 // Roots of the batch's sets, reached at level 0.  <<<1, 32>>>
 __global__ void ms_start_kernel(MsArgs a) {
     const uint32_t s = threadIdx.x;
-    if (s < a.mc->nsets) {
+    if (s < a.mc->nsets && a.sets[s] != NONE) {  // NONE: an unused slot of a tile batch
         const uint4 rr = philox4x32_10(make_uint4(0u, a.sets[s], a.epoch, STREAM_ROOT), a.key0, a.key1);
         atomicOr(&a.nxt[__umulhi(rr.x, a.g.n)], 1u << s);
     }
@@ -203,22 +259,29 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
         w_ee[warp][lane] = e;
         w_f[warp][lane] = f;
         __syncwarp();
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t t = base + lane;
-            uint32_t gg = 0, eb = 0, ee = 0, ff = 0;
-            if (t < total) {
-                uint32_t lo = 0, hi = 31;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (w_scan[warp][mid] > t) hi = mid;
-                    else lo = mid + 1;
+        for (uint32_t base = 0; base < total; base += MS_ROUND) {
+            bool ok[2];
+            uint32_t gg[2], eb[2], ee[2], ff[2];
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                // consecutive lanes take consecutive groups (coalesced loads)
+                const uint32_t t = base + 32 * k + lane;
+                ok[k] = t < total;
+                gg[k] = eb[k] = ee[k] = ff[k] = 0;
+                if (ok[k]) {
+                    uint32_t lo = 0, hi = 31;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (w_scan[warp][mid] > t) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    gg[k] = w_g0[warp][lo] + (t - (lo ? w_scan[warp][lo - 1] : 0u));
+                    eb[k] = w_eb[warp][lo];
+                    ee[k] = w_ee[warp][lo];
+                    ff[k] = w_f[warp][lo];
                 }
-                gg = w_g0[warp][lo] + (t - (lo ? w_scan[warp][lo - 1] : 0u));
-                eb = w_eb[warp][lo];
-                ee = w_ee[warp][lo];
-                ff = w_f[warp][lo];
             }
-            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, t < total, gg, eb, ee, ff);
+            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, ok, gg, eb, ee, ff);
         }
         __syncwarp();
     }
@@ -237,8 +300,12 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_heavy_kernel(MsArgs a) {
     for (uint32_t it = blockIdx.x * MS_WARPS + warp; it < nH; it += gridDim.x * MS_WARPS) {
         const uint4 item = a.heavy[it];  // one chunk per warp
         const uint32_t eb = __ldg(a.g.row_ptr + item.x), ee = __ldg(a.g.row_ptr + item.x + 1);
-        for (uint32_t g = item.y; g < item.z; g += 32)
-            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, g + lane < item.z, g + lane, eb, ee, item.w);
+        for (uint32_t g = item.y; g < item.z; g += MS_ROUND) {
+            const bool ok[2] = {g + lane < item.z, g + 32 + lane < item.z};
+            const uint32_t gg[2] = {g + lane, g + 32 + lane}, ebs[2] = {eb, eb}, ees[2] = {ee, ee};
+            const uint32_t ff[2] = {item.w, item.w};
+            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, ok, gg, ebs, ees, ff);
+        }
     }
     ms_flush_live(a, s_live, nblk);
 }
@@ -396,6 +463,53 @@ __global__ void ms_commit_kernel(MsArgs a, uint32_t dense, uint32_t mode, uint64
     }
 }
 
+// Vertex-major tile of a Bitmax pool (Section 4.2.3, Eq. (3)): the batch's
+// slots are the tile's columns, so the visited masks are the tile's words;
+// they are ORed into it (a tile may be filled over several batches) and
+// cleared.
+__global__ void __launch_bounds__(MS_THREADS) ms_tile_emit_kernel(MsArgs a, uint32_t* tile) {
+    const uint32_t n4 = (a.g.n + 3) / 4;
+    uint4* vis4 = reinterpret_cast<uint4*>(a.vis);
+    uint4* t4 = reinterpret_cast<uint4*>(tile);
+    for (uint32_t q = blockIdx.x * MS_THREADS + threadIdx.x; q < n4; q += gridDim.x * MS_THREADS) {
+        const uint4 m = vis4[q];
+        if (m.x | m.y | m.z | m.w) {
+            const uint4 o = t4[q];
+            t4[q] = make_uint4(o.x | m.x, o.y | m.y, o.z | m.z, o.w | m.w);
+            vis4[q] = make_uint4(0, 0, 0, 0);
+        }
+    }
+}
+
+// Records and pool counters of a tile batch's sets (slot s = set 32t + s for
+// the slots in `slots`); new_words: heap words the batch's tile adds (its
+// first batch).  <<<1, 32>>>
+__global__ void ms_tile_commit_kernel(MsArgs a, uint32_t slots, uint64_t tile_off, uint64_t new_words) {
+    const uint32_t s = threadIdx.x;
+    const bool on = (slots >> s) & 1u;
+    unsigned long long verts = 0, sc = 0, lv = 0;
+    if (on) {
+        a.recs[a.sets[s]] = make_rec(KIND_BITMAP, tile_off, (uint32_t)a.mc->size[s], 0);
+        verts = a.mc->size[s];
+        sc = a.mc->scanned[s];
+        lv = a.mc->live[s];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        verts += __shfl_xor_sync(0xFFFFFFFFu, verts, o);
+        sc += __shfl_xor_sync(0xFFFFFFFFu, sc, o);
+        lv += __shfl_xor_sync(0xFFFFFFFFu, lv, o);
+    }
+    if (s == 0) {
+        const unsigned long long nd = (unsigned long long)__popc(slots);
+        atomicAdd(&a.ctr->sets_bm, nd);
+        atomicAdd(&a.ctr->sets_big, nd);
+        atomicAdd(&a.ctr->rr_vertices, verts);
+        if (new_words) atomicAdd(&a.ctr->words_used, (unsigned long long)new_words);
+        if (sc) atomicAdd(&a.ctr->edges_scanned, sc);
+        if (lv) atomicAdd(&a.ctr->edges_live, lv);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
@@ -430,6 +544,13 @@ cudaError_t launch_ms_finish(const MsArgs& a, int sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_ms_tile(const MsArgs& a, uint32_t slots, uint32_t* bm_heap, uint64_t tile_off,
+                           uint64_t new_words, int sms, cudaStream_t s) {
+    ms_tile_emit_kernel<<<(uint32_t)sms * 4, MS_THREADS, 0, s>>>(a, bm_heap + tile_off);
+    ms_tile_commit_kernel<<<1, 32, 0, s>>>(a, slots, tile_off, new_words);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ms_emit(const MsArgs& a, uint32_t dense, uint32_t mode, uint64_t row_words, uint32_t* bm_heap,
                            int sms, cudaStream_t s) {
     ms_emit_kernel<<<(uint32_t)sms * 2, MS_THREADS, 0, s>>>(a, mode == MODE_ENCODE ? dense : 0u, bm_heap);
@@ -447,19 +568,18 @@ cudaError_t launch_ms_emit(const MsArgs& a, uint32_t dense, uint32_t mode, uint6
 // ---------------------------------------------------------------------------
 namespace hbx {
 
-__global__ void __launch_bounds__(256) philox_ceiling_kernel(uint32_t per_thread, uint32_t key0, uint32_t key1,
-                                                             uint32_t* out) {
+__global__ void __launch_bounds__(256) philox_ceiling_kernel(uint32_t per_thread, PhiloxKeys rk, uint32_t* out) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t acc = 0;
     for (uint32_t i = 0; i < per_thread; i++) {
-        const uint4 x = philox4x32_10(make_uint4(i, tid, 0u, STREAM_IC), key0, key1);
+        const uint4 x = philox4x32_10_rk(make_uint4(i, tid, 0u, STREAM_IC), rk);
         acc ^= x.x ^ x.y ^ x.z ^ x.w;
     }
     out[tid] = acc;
 }
 
 cudaError_t launch_philox_ceiling(uint32_t blocks, uint32_t per_thread, uint32_t* out, cudaStream_t s) {
-    philox_ceiling_kernel<<<blocks, 256, 0, s>>>(per_thread, 0x243F6A88u, 0x85A308D3u, out);
+    philox_ceiling_kernel<<<blocks, 256, 0, s>>>(per_thread, philox_round_keys(0x243F6A88u, 0x85A308D3u), out);
     return cudaGetLastError();
 }
 

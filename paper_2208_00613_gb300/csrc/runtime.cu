@@ -132,6 +132,8 @@ extern "C" void hbx_default_options(hbx_options* o) {
     o->wait_cycles = 0;
     o->scheme = 0;
     o->select_mode = 0;
+    o->fresh_final = 0;
+    o->reserved_opt = 0;
 }
 
 extern "C" int hbx_create(hbx_ctx** out, int dev, void* stream) {
@@ -463,6 +465,7 @@ static SampleArgs sample_args(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t 
     a.g = dev_graph(p->g);
     a.key0 = (uint32_t)p->seed;
     a.key1 = (uint32_t)(p->seed >> 32);
+    a.rk = philox_round_keys(a.key0, a.key1);
     a.epoch = p->o.pool_epoch;
     a.model = (uint32_t)p->model;
     a.mode = mode;
@@ -558,6 +561,7 @@ static MsArgs ms_args(hbx_pool* p) {
     a.col4 = p->g->col;  // allocated with 16 zero bytes past m entries
     a.key0 = (uint32_t)p->seed;
     a.key1 = (uint32_t)(p->seed >> 32);
+    a.rk = philox_round_keys(a.key0, a.key1);
     a.epoch = p->o.pool_epoch;
     a.sets = p->ms_sets;
     a.vis = p->ms_vis;
@@ -597,6 +601,41 @@ static int ensure_ms_graphs(hbx_pool* p, const MsArgs& a) {
     return HBX_OK;
 }
 
+// One batch of the bit-parallel search: the listed sets (NONE = an unused
+// slot) searched to the end; their sizes and edge counts come back in *mc.
+// With `timed`, an event pair opens around the batch (closed by the caller).
+static int ms_search_batch(hbx_pool* p, const uint32_t* ids, uint32_t nb, bool timed, MsCounters* mc) {
+    hbx_ctx* ctx = p->ctx;
+    const uint32_t n = p->g->n;
+    CK(cudaMemcpyAsync(p->ms_sets, ids, (size_t)nb * 4, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemsetAsync(p->ms_c, 0, sizeof(MsCounters), p->stream));
+    CK(cudaMemcpyAsync(&p->ms_c->nsets, &nb, 4, cudaMemcpyHostToDevice, p->stream));
+    const MsArgs a = ms_args(p);
+    RC(ensure_ms_graphs(p, a));
+    if (timed) CK(cudaEventRecord(p->ev0, p->stream));
+    // the levels run from CUDA graphs of MS_GRAPH_LEVELS levels each, the
+    // first one preceded by the roots; the host looks at the frontier after
+    // each graph
+    for (uint64_t level = 0;; level += MS_GRAPH_LEVELS) {
+        if (level > (uint64_t)n) return fail(ctx, HBX_ERR_INTERNAL, "bit-parallel search did not end");
+        CK(cudaGraphLaunch(level ? p->ms_more : p->ms_first, p->stream));
+        p->launches += (level ? 0 : 3) + 4 * MS_GRAPH_LEVELS;
+        uint32_t nF = 0;
+        CK(cudaMemcpyAsync(&nF, &p->ms_c->nF, 4, cudaMemcpyDeviceToHost, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+        if (nF == 0) break;
+    }
+    CK(launch_ms_finish(a, ctx->sms, p->stream));
+    p->launches++;
+    CK(cudaMemcpyAsync(mc, p->ms_c, sizeof(*mc), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    if (timed) {
+        p->ms_nsets += nb;
+        p->ms_blocks += mc->blocks;
+    }
+    return HBX_OK;
+}
+
 // Sample the listed IC sets (ids on the host) MS_SETS at a time with the
 // bit-parallel search.  Dense sets are stored as bitmap rows (MODE_ENCODE) or
 // counted (MODE_HIST); each of the others is encoded (or histogrammed) by one
@@ -609,33 +648,9 @@ static int run_multi_source(hbx_pool* p, uint32_t mode, uint32_t cut, const std:
     const uint32_t n = p->g->n;
     for (size_t b0 = 0; b0 < ids.size(); b0 += MS_SETS) {
         const uint32_t nb = (uint32_t)std::min<size_t>(MS_SETS, ids.size() - b0);
-        CK(cudaMemcpyAsync(p->ms_sets, ids.data() + b0, (size_t)nb * 4, cudaMemcpyHostToDevice, p->stream));
-        CK(cudaMemsetAsync(p->ms_c, 0, sizeof(MsCounters), p->stream));
-        CK(cudaMemcpyAsync(&p->ms_c->nsets, &nb, 4, cudaMemcpyHostToDevice, p->stream));
-        const MsArgs a = ms_args(p);
-        RC(ensure_ms_graphs(p, a));
-        if (timed) CK(cudaEventRecord(p->ev0, p->stream));
-        // the levels run from CUDA graphs of MS_GRAPH_LEVELS levels each, the
-        // first one preceded by the roots; the host looks at the frontier
-        // after each graph
-        for (uint64_t level = 0;; level += MS_GRAPH_LEVELS) {
-            if (level > (uint64_t)n) return fail(ctx, HBX_ERR_INTERNAL, "bit-parallel search did not end");
-            CK(cudaGraphLaunch(level ? p->ms_more : p->ms_first, p->stream));
-            p->launches += (level ? 0 : 3) + 4 * MS_GRAPH_LEVELS;
-            uint32_t nF = 0;
-            CK(cudaMemcpyAsync(&nF, &p->ms_c->nF, 4, cudaMemcpyDeviceToHost, p->stream));
-            CK(cudaStreamSynchronize(p->stream));
-            if (nF == 0) break;
-        }
-        CK(launch_ms_finish(a, ctx->sms, p->stream));
-        p->launches++;
         MsCounters mc;
-        CK(cudaMemcpyAsync(&mc, p->ms_c, sizeof(mc), cudaMemcpyDeviceToHost, p->stream));
-        CK(cudaStreamSynchronize(p->stream));
-        if (timed) {
-            p->ms_nsets += nb;
-            p->ms_blocks += mc.blocks;
-        }
+        RC(ms_search_batch(p, ids.data() + b0, nb, timed, &mc));
+        const MsArgs a = ms_args(p);
         uint32_t dense = 0, nd = 0, nsp = 0;
         unsigned long long rowoff[MS_SETS] = {0};
         uint32_t sparse[2 * MS_SETS];  // mask bits, then set ids, of the sets under the cut
@@ -989,7 +1004,7 @@ static int characterize(hbx_pool* p) {
     const uint32_t n = p->g->n;
     if (p->bitmax) {
         p->cut = n + 1;
-        p->tiles = p->model == HBX_IC;
+        p->tiles = p->model == HBX_IC && p->o.form == 1;
         p->hist_dense = W;
         p->hist_verts = 0;
     } else {
@@ -1075,11 +1090,49 @@ static int reserve_heaps(hbx_pool* p, uint64_t count) {
     return HBX_OK;
 }
 
-// Sets [j0, j0 + count) of a Bitmax IC pool as vertex-major tiles.
+// Sets [j0, j0 + count) of a Bitmax IC pool, as the vertex-major bit matrix
+// of Section 4.2.3 / Eq. (3): tile t (at word t * n4 of the bitmap heap, n4 =
+// n rounded up to 4) holds sets [32t, 32t + 32), word v bit s for set 32t + s.
+// Every set is found by the bit-parallel search, one tile's sets per batch, so
+// the search's visited masks are the tile's words.
 static int run_tiles(hbx_pool* p, uint32_t j0, uint32_t count) {
-    (void)j0;
-    (void)count;
-    return fail(p->ctx, HBX_ERR_INVALID_ARG, "vertex-major tiles: not available");
+    hbx_ctx* ctx = p->ctx;
+    RC(ensure_ms_scratch(p));
+    const uint64_t n4 = ((uint64_t)p->g->n + 3) & ~3ull;
+    const uint64_t jend = (uint64_t)j0 + count;
+    for (uint64_t j = j0; j < jend;) {
+        const uint64_t t = j / 32;
+        const uint32_t s0 = (uint32_t)(j % 32), s1 = (uint32_t)std::min<uint64_t>(32, s0 + (jend - j));
+        uint32_t ids[MS_SETS];
+        uint32_t slots = 0;
+        for (uint32_t s = 0; s < MS_SETS; s++) {
+            const bool on = s >= s0 && s < s1;
+            ids[s] = on ? (uint32_t)(32 * t + s) : NONE;
+            if (on) slots |= 1u << s;
+        }
+        MsCounters mc;
+        RC(ms_search_batch(p, ids, MS_SETS, true, &mc));
+        const uint64_t off = t * n4;
+        const bool fresh = off + n4 > p->hc.bm_cursor;  // the tile's first batch
+        if (fresh) {
+            RC(grow_heap(p, p->bm, off + n4));
+            const unsigned long long cursor = off + n4;
+            CK(cudaMemcpyAsync(&p->ctr->bm_cursor, &cursor, 8, cudaMemcpyHostToDevice, p->stream));
+            p->hc.bm_cursor = cursor;
+        }
+        const MsArgs a = ms_args(p);
+        CK(launch_ms_tile(a, slots, p->bm.d, off, fresh ? n4 : 0, ctx->sms, p->stream));
+        p->launches += 2;
+        CK(cudaEventRecord(p->ev1, p->stream));
+        CK(cudaEventSynchronize(p->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        p->sample_kernel_s += ms * 1e-3;
+        p->ms_kernel_s += ms * 1e-3;
+        p->sample_kernel_launches++;
+        j += s1 - s0;
+    }
+    return read_counters(p);
 }
 
 int pool_extend(hbx_pool* p, uint64_t T) {
@@ -1146,12 +1199,20 @@ static int ensure_sel(hbx_pool* p, uint64_t T, uint32_t k) {
         RC(grow_buffer(p, (void**)&p->ticket, 0, 256, 0));
     }
     if (T > p->alive_cap) {
-        const uint64_t nc = std::max<uint64_t>(T, p->alive_cap * 2);
+        // a multiple of 32: a tile's 32 live flags are read as two 16-byte words
+        const uint64_t nc = (std::max<uint64_t>(T, p->alive_cap * 2) + 31) & ~31ull;
         RC(grow_buffer(p, (void**)&p->alive, p->alive_cap, nc, 0));
         RC(grow_buffer(p, (void**)&p->cov_huff, p->alive_cap * 4, nc * 4, 0));
         RC(grow_buffer(p, (void**)&p->cov_bm, p->alive_cap * 4, nc * 4, 0));
         RC(grow_buffer(p, (void**)&p->cov_raw, p->alive_cap * 4, nc * 4, 0));
+        if (p->tiles) RC(grow_buffer(p, (void**)&p->tile_live, p->alive_cap / 8, nc / 8, 0));
         p->alive_cap = nc;
+    }
+    if (p->tiles && (T + 31) / 32 > p->dec_cap) {
+        // one decrement entry per covered tile
+        const uint64_t nc = std::max<uint64_t>((T + 31) / 32, p->dec_cap * 2);
+        RC(grow_buffer(p, (void**)&p->dec_items, p->dec_cap * 8, nc * 8, 0));
+        p->dec_cap = nc;
     }
     if (p->hc.chunk_items > p->dec_cap) {
         // the sets covered in one iteration hold at most every chunk of the pool
@@ -1198,6 +1259,10 @@ static SelArgs sel_args(hbx_pool* p, uint64_t T) {
     a.marginal = p->d_marg;
     a.sms = p->ctx->sms;
     a.wait_cycles = p->o.wait_cycles ? (long long)std::min<uint64_t>(p->o.wait_cycles, 1ull << 62) : 4000000000ll;
+    a.select_mode = p->o.select_mode;
+    a.tiles = p->tiles ? 1u : 0u;
+    a.n4w = ((uint64_t)p->g->n + 3) & ~3ull;
+    a.tile_live = p->tile_live;
     return a;
 }
 
@@ -1210,13 +1275,19 @@ static SelBarrier* sel_barrier(hbx_pool* p) {
 // Launch greedy selection on sets [0, T) on stream `st` without waiting.  The
 // batched form runs the k iterations in one persistent cooperative launch; the
 // plain form launches them one by one and reads u* back after each.
-static int pool_select_launch(hbx_pool* p, uint64_t T, uint32_t k, cudaStream_t st) {
+static int pool_select_launch(hbx_pool* p, uint64_t T, uint32_t k, cudaStream_t st, uint64_t j_lo = 0) {
     hbx_ctx* ctx = p->ctx;
     if (T == 0 || T > p->T) return fail(ctx, HBX_ERR_INVALID_ARG, "T must be in [1, pool size]");
     if (k == 0 || k > p->g->n) return fail(ctx, HBX_ERR_INVALID_ARG, "k must be in [1, n]");
+    if (j_lo >= T) return fail(ctx, HBX_ERR_INVALID_ARG, "a selection range must start below T");
+    // the last batch end at or below j_lo (the count passes skip sets below j_lo)
+    auto lo_bd = p->bounds.upper_bound(j_lo);
+    const bool lo_known = lo_bd != p->bounds.begin();
+    if (lo_known) --lo_bd;
     cudaSetDevice(ctx->device);
     RC(ensure_sel(p, T, k));
-    const SelArgs a = sel_args(p, T);
+    SelArgs a = sel_args(p, T);
+    a.j_lo = (uint32_t)j_lo;  // sets below j_lo start covered
     const uint32_t enc = p->o.encode;
     CK(launch_sel_init(a, st));
     // The batched form counts incrementally: the undecremented counts of the
@@ -1227,7 +1298,16 @@ static int pool_select_launch(hbx_pool* p, uint64_t T, uint32_t k, cudaStream_t 
     const size_t cbytes = (size_t)a.n4 * 4;
     const auto bd = p->bounds.find(p->base_T);
     uint64_t words_lo = 0;
-    if (p->o.form && p->base_T && p->base_T <= T && bd != p->bounds.end()) {
+    if (j_lo) {
+        // a range [j_lo, T): counted from scratch
+        if (lo_known) {
+            c.chunk_items = p->items + lo_bd->second.items;
+            c.n_items = a.n_items - lo_bd->second.items;
+            c.bm_sets = p->bm_sets + lo_bd->second.bm;
+            c.n_bm = a.n_bm - (uint32_t)lo_bd->second.bm;
+            words_lo = lo_bd->second.words;
+        }
+    } else if (p->o.form && p->base_T && p->base_T <= T && bd != p->bounds.end()) {
         CK(cudaMemcpyAsync(p->cnt, p->cnt_base, cbytes, cudaMemcpyDeviceToDevice, st));
         c.chunk_items = p->items + bd->second.items;
         c.n_items = a.n_items - bd->second.items;
@@ -1252,7 +1332,7 @@ static int pool_select_launch(hbx_pool* p, uint64_t T, uint32_t k, cudaStream_t 
         p->count_bytes += 4 * (words_hi - std::min(words_hi, words_lo)) + 16 * (T - c.j_lo) + 8 * c.n_items +
                           4ull * c.n_bm;
     }
-    if (p->o.form && p->bounds.count(T)) {
+    if (p->o.form && p->bounds.count(T) && !j_lo) {
         if (!p->cnt_base) RC(grow_buffer(p, (void**)&p->cnt_base, 0, cbytes, 0));
         CK(cudaMemcpyAsync(p->cnt_base, p->cnt, cbytes, cudaMemcpyDeviceToDevice, st));
         p->base_T = T;
@@ -1303,7 +1383,7 @@ static int pool_select_finish(hbx_pool* p, uint32_t k, uint32_t* seeds, uint64_t
     }
     p->select_iterations += hs.it;
     p->dec_bytes += hs.dec_bytes;
-    p->dec_s += 1e-9 * (double)hs.t_dec_ns;
+    p->dec_s += 1e-9 * (double)(hs.t_cover_ns + hs.t_dec_ns);
     if (hs.pad == 1) return fail(ctx, HBX_ERR_INTERNAL, "undecodable Huffman stream during selection");
     if (hs.pad) return fail(ctx, HBX_ERR_INTERNAL, "decrement item list overflow during selection");
     if (hs.it != k) return fail(ctx, HBX_ERR_INTERNAL, "selection ran " + std::to_string(hs.it) + " iterations");
@@ -1313,9 +1393,10 @@ static int pool_select_finish(hbx_pool* p, uint32_t k, uint32_t* seeds, uint64_t
     return HBX_OK;
 }
 
-int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* marginal, uint64_t* covered) {
+int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* marginal, uint64_t* covered,
+                uint64_t j_lo) {
     const double t0 = now_s();
-    RC(pool_select_launch(p, T, k, p->stream));
+    RC(pool_select_launch(p, T, k, p->stream, j_lo));
     RC(pool_select_finish(p, k, seeds, marginal, covered, p->stream));
     p->select_s += now_s() - t0;
     return HBX_OK;
@@ -1340,7 +1421,8 @@ extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint
         return fail(ctx, HBX_ERR_INVALID_ARG, "warp_capacity must be a power of two in [64, 2048]");
     if (o.block_cluster > 8 || (o.block_cluster & (o.block_cluster - 1)))
         return fail(ctx, HBX_ERR_INVALID_ARG, "block_cluster must be 0, 1, 2, 4 or 8");
-    if (o.scheme > 1 || o.select_mode > 1) return fail(ctx, HBX_ERR_INVALID_ARG, "scheme and select_mode are 0 or 1");
+    if (o.scheme > 1 || o.select_mode > 1 || o.fresh_final > 1)
+        return fail(ctx, HBX_ERR_INVALID_ARG, "scheme, select_mode and fresh_final are 0 or 1");
     if (o.scheme && !o.encode) return fail(ctx, HBX_ERR_INVALID_ARG, "the per-graph scheme needs encode = 1");
     if (g->n >= 0xFFFFFFFFu && o.scheme) return fail(ctx, HBX_ERR_INVALID_ARG, "graph too large for the Bitmax cut");
     cudaSetDevice(ctx->device);
@@ -1381,7 +1463,7 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
                     p->retry_list, p->list_in, p->giant_list, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
                     p->alive, p->cov_huff, p->cov_bm, p->cov_raw, p->st, p->partials, p->ticket, p->d_seeds,
                     p->d_marg, p->dec_items, p->cnt_base, p->ms_vis, p->ms_nxt, p->ms_F, p->ms_N,
-                    p->ms_heavy, p->ms_c, p->ms_sets, p->ms_rowoff, p->ms_sparse};
+                    p->ms_heavy, p->ms_c, p->ms_sets, p->ms_rowoff, p->ms_sparse, p->tile_live};
     for (void* b : bufs) dfree(c, b);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
@@ -1504,6 +1586,8 @@ void fill_stats(hbx_pool* p, hbx_stats* s) {
     s->dec_s = p->dec_s;
     s->dec_bytes = p->dec_bytes;
     s->uncoded_vertices = p->hc.uncoded;
+    s->scheme = !p->o.scheme ? 0u : (!p->bitmax ? 1u : (p->tiles ? 3u : 2u));
+    s->scheme_skewness = p->scheme_skew;
 }
 
 int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds, double* influence,
@@ -1544,10 +1628,12 @@ int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds
         }
     }
     uint64_t T = (uint64_t)std::ceil(b.lambda_star / LB);
-    if (T < Ti) T = Ti;
-    RC(pool_extend(p, T));
     uint64_t cov = 0;
-    if (T == last_T) {
+    if (p->o.fresh_final) {
+        // the final phase on theta new sets [T_i, T_i + theta)
+        RC(pool_extend(p, Ti + T));
+        RC(pool_select(p, Ti + T, k, seeds, marginal, &cov, Ti));
+    } else if ((T = std::max(T, Ti)) == last_T) {
         // greedy selection is a function of the sets [0, T): the last round's
         // result is the final one
         for (uint32_t i = 0; i < k; i++) seeds[i] = last_seeds[i];
@@ -1555,6 +1641,7 @@ int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds
             for (uint32_t i = 0; i < k; i++) marginal[i] = last_marg[i];
         cov = last_cov;
     } else {
+        RC(pool_extend(p, T));
         RC(pool_select(p, T, k, seeds, marginal, &cov));
     }
     *influence = dn * (double)cov / (double)T;
@@ -1623,6 +1710,7 @@ static int decode_range(hbx_pool* p, uint64_t j0, uint64_t j1, const uint64_t* o
     a.out = d_out;
     a.ends = d_end;
     a.ctr = p->ctr;
+    a.tiles = p->tiles ? 1u : 0u;
     cudaError_t e = cudaMemcpyAsync(d_off, offsets, (cnt + 1) * 8, cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_end, 0, cnt * 8, p->stream);
     if (e == cudaSuccess) e = launch_decode(a, p->stream);
@@ -1681,10 +1769,21 @@ extern "C" int hbx_pool_export_set(hbx_pool* p, uint64_t j, uint32_t* kind, uint
         CK(cudaStreamSynchronize(p->stream));
         memcpy(buf.data(), words.data(), cb);
     } else if (k == KIND_BITMAP) {
-        const uint64_t nw = ((uint64_t)p->g->n + 31) / 32;
-        buf.resize(nw * 4);
-        CK(cudaMemcpyAsync(buf.data(), p->bm.d + off, nw * 4, cudaMemcpyDeviceToHost, p->stream));
-        CK(cudaStreamSynchronize(p->stream));
+        const uint32_t n = p->g->n;
+        const uint64_t nw = ((uint64_t)n + 31) / 32;
+        buf.assign(nw * 4, 0);
+        if (p->tiles) {
+            // column j % 32 of a vertex-major tile
+            std::vector<uint32_t> tile(n);
+            CK(cudaMemcpyAsync(tile.data(), p->bm.d + off, (size_t)n * 4, cudaMemcpyDeviceToHost, p->stream));
+            CK(cudaStreamSynchronize(p->stream));
+            uint32_t* row = reinterpret_cast<uint32_t*>(buf.data());
+            for (uint32_t v = 0; v < n; v++)
+                if ((tile[v] >> (j & 31)) & 1u) row[v >> 5] |= 1u << (v & 31);
+        } else {
+            CK(cudaMemcpyAsync(buf.data(), p->bm.d + off, nw * 4, cudaMemcpyDeviceToHost, p->stream));
+            CK(cudaStreamSynchronize(p->stream));
+        }
     } else {
         buf.resize(4ull * r.size);
         CK(cudaMemcpyAsync(buf.data(), p->raw.d + off, 4ull * r.size, cudaMemcpyDeviceToHost, p->stream));

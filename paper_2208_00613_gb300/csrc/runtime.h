@@ -135,6 +135,7 @@ struct hbx_pool {
     uint8_t* alive = nullptr;
     uint64_t alive_cap = 0;
     uint32_t *cov_huff = nullptr, *cov_bm = nullptr, *cov_raw = nullptr;
+    uint32_t* tile_live = nullptr;  // tile pools: live-set mask per tile (recount)
     unsigned long long* dec_items = nullptr;  // chunk items of the sets covered in one iteration
     uint64_t dec_cap = 0;
     void* st = nullptr;
@@ -160,7 +161,9 @@ int cuda_fail(hbx_ctx* c, cudaError_t e, const char* what);
 int dalloc(hbx_ctx* c, void** p, size_t bytes);
 void dfree(hbx_ctx* c, void* p);
 int pool_extend(hbx_pool* p, uint64_t T);
-int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* marginal, uint64_t* covered);
+// greedy on sets [j_lo, T) (j_lo = 0 or a batch end of the pool)
+int pool_select(hbx_pool* p, uint64_t T, uint32_t k, uint32_t* seeds, uint64_t* marginal, uint64_t* covered,
+                uint64_t j_lo = 0);
 int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds, double* influence,
                 uint64_t* marginal, hbx_stats* stats);
 void fill_stats(hbx_pool* p, hbx_stats* s);

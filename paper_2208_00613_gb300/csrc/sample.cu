@@ -91,7 +91,7 @@ __device__ __forceinline__ bool hash_insert(uint32_t* h, uint32_t mask, uint32_t
 __device__ __forceinline__ uint32_t group_coins(const SampleArgs& a, uint32_t j, uint32_t gg, uint32_t eb,
                                                 uint32_t ee, unsigned long long* scanned) {
     const uint4 t4 = __ldg(reinterpret_cast<const uint4*>(a.g.thr) + gg);
-    const uint4 x = philox4x32_10(make_uint4(gg, j, a.epoch, STREAM_IC), a.key0, a.key1);
+    const uint4 x = philox4x32_10_rk(make_uint4(gg, j, a.epoch, STREAM_IC), a.rk);
     const uint32_t e0 = gg * 4u;
     const bool v0 = e0 >= eb && e0 < ee, v1 = e0 + 1 >= eb && e0 + 1 < ee;
     const bool v2 = e0 + 2 >= eb && e0 + 2 < ee, v3 = e0 + 3 >= eb && e0 + 3 < ee;

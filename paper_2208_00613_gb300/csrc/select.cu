@@ -58,7 +58,7 @@ __device__ __forceinline__ HuffView huff_view(const uint32_t* code_heap, const S
 __global__ void sel_init_kernel(SelArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n4; v += stride) a.cnt[v] = v < a.n ? 0 : -1;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < a.T; j += stride) a.alive[j] = 1;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < a.T; j += stride) a.alive[j] = j >= a.j_lo;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         SelState z;
         z.u = NONE; z.it = 0; z.n_cov_huff = 0; z.n_cov_bm = 0; z.n_cov_raw = 0; z.pad = 0; z.gain = 0; z.covered = 0;
@@ -76,39 +76,36 @@ __global__ void sel_init_kernel(SelArgs a) {
 // same counter.  The item count comes from the device (n_dev) or the host.
 // ---------------------------------------------------------------------------
 
-// Items [wb, wb + 32) of `items`, one per lane of the calling warp (all lanes
-// call it).  Items are read through L2: the decrement lists are written by
-// other blocks of the same persistent launch.
-__device__ __forceinline__ void count_items_warp(const SelArgs& a, const DecodeSmem& ds, uint32_t* hist, uint32_t hot,
-                                                 const unsigned long long* items, unsigned long long n_items,
-                                                 unsigned long long wb, int sign) {
+// Chunk c of Huffman set j, one per lane of the calling warp (all lanes call
+// it; valid = false: no chunk): its 32 codes (or 32 copy-array ids) are
+// decoded and each vertex's count moves by `sign` -- hot ranks in the block's
+// shared histogram, the rest in cnt, one atomic per group of lanes that hit
+// the same counter.  alive_only (recount) skips sets not alive; sets outside
+// [j_lo, T) are skipped.
+__device__ __forceinline__ void count_chunk_warp(const SelArgs& a, const DecodeSmem& ds, uint32_t* hist, uint32_t hot,
+                                                 bool valid, uint32_t j, uint32_t c, int sign,
+                                                 const uint8_t* alive_only = nullptr) {
     const uint32_t lane = threadIdx.x & 31;
-    const unsigned long long t = wb + lane;
     uint32_t ncodes = 0, is_code = 0;
     uint64_t pos = 0, pos0 = 0;
     const uint32_t* words = nullptr;
     const uint32_t* raw = nullptr;
-    if (t < n_items) {
-        const unsigned long long item = __ldcg(items + t);
-        const uint32_t j = (uint32_t)(item >> 32), c = (uint32_t)item;
-        if (j < a.T) {
-            const HuffView h = huff_view(a.code_heap, a.recs[j]);
-            const uint32_t nch = (h.n_coded + 31) / 32;
-            if (c < nch) {
-                words = h.words;
-                pos = c ? h.side[c - 1] : 0u;
-                pos0 = pos;
-                ncodes = min(32u, h.n_coded - 32 * c);
-                is_code = 1;
-            } else {
-                const uint32_t rc = c - nch;
-                raw = h.raw + 32ull * rc;
-                ncodes = min(32u, h.n_raw - 32 * rc);
-            }
+    if (valid && j < a.T && j >= a.j_lo && (!alive_only || __ldcg(alive_only + j))) {
+        const HuffView h = huff_view(a.code_heap, a.recs[j]);
+        const uint32_t nch = (h.n_coded + 31) / 32;
+        if (c < nch) {
+            words = h.words;
+            pos = c ? h.side[c - 1] : 0u;
+            pos0 = pos;
+            ncodes = min(32u, h.n_coded - 32 * c);
+            is_code = 1;
+        } else {
+            const uint32_t rc = c - nch;
+            raw = h.raw + 32ull * rc;
+            ncodes = min(32u, h.n_raw - 32 * rc);
         }
     }
-    uint32_t i = 0;
-    for (; i < 32; i++) {
+    for (uint32_t i = 0; i < 32; i++) {
         const bool have = i < ncodes;
         uint32_t target = NONE;
         if (have) {
@@ -117,25 +114,38 @@ __device__ __forceinline__ void count_items_warp(const SelArgs& a, const DecodeS
                 if (r == NONE) atomicMax(&a.st->pad, 1u);
                 else target = r < hot ? r : (RAW_FLAG | __ldg(a.cb.vertex_of_rank + r));
             } else {
-                target = RAW_FLAG | raw[i];
+                target = RAW_FLAG | __ldg(raw + i);
             }
         }
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, target);
         if (have && target != NONE && lane == (uint32_t)(__ffs(peers) - 1)) {
-            const uint32_t c = __popc(peers);
-            if (target & RAW_FLAG) atomicAdd(&a.cnt[target & ~RAW_FLAG], sign * (int)c);
-            else atomicAdd(&hist[target], c);
+            const uint32_t n = __popc(peers);
+            if (target & RAW_FLAG) atomicAdd(&a.cnt[target & ~RAW_FLAG], sign * (int)n);
+            else atomicAdd(&hist[target], n);
         }
         if (__all_sync(0xFFFFFFFFu, i + 1 >= ncodes)) break;
     }
     if (sign < 0) {
-        // bytes this decrement read: the item, the chunk's code bits (with its
+        // bytes this decrement read: the chunk item, its code bits (with the
         // side entry) or copy-array ids
         uint32_t by = 0;
-        if (t < n_items) by = 8u + (is_code ? (uint32_t)((pos - pos0 + 7) / 8) + 4u : 4u * ncodes);
+        if (ncodes) by = 8u + (is_code ? (uint32_t)((pos - pos0 + 7) / 8) + 4u : 4u * ncodes);
         by = warp_sum(by);
         if (lane == 0 && by) atomicAdd(&a.st->dec_bytes, (unsigned long long)by);
     }
+}
+
+// Items [wb, wb + 32) of `items` ((j << 32) | chunk), one per lane of the
+// calling warp (all lanes call it).  Items are read through L2: decrement
+// lists are written by other blocks of the same persistent launch.
+__device__ __forceinline__ void count_items_warp(const SelArgs& a, const DecodeSmem& ds, uint32_t* hist, uint32_t hot,
+                                                 const unsigned long long* items, unsigned long long n_items,
+                                                 unsigned long long wb, int sign,
+                                                 const uint8_t* alive_only = nullptr) {
+    const unsigned long long t = wb + (threadIdx.x & 31);
+    unsigned long long item = 0;
+    if (t < n_items) item = __ldcg(items + t);
+    count_chunk_warp(a, ds, hist, hot, t < n_items, (uint32_t)(item >> 32), (uint32_t)item, sign, alive_only);
 }
 
 __global__ void __launch_bounds__(COUNT_THREADS) count_items_kernel(SelArgs a, const unsigned long long* items,
@@ -205,7 +215,8 @@ struct Planes {
 // for every bit with a nonzero count.  Rows are padded to a multiple of 4 words
 // and 16-byte aligned.  All threads of the block call it with the same tile.
 __device__ __forceinline__ void bitmap_tile(const SelArgs& a, const uint32_t* list, uint32_t len, uint64_t tile,
-                                            int sign, unsigned long long* s_off, uint32_t* s_n) {
+                                            int sign, unsigned long long* s_off, uint32_t* s_n,
+                                            const uint8_t* alive_only = nullptr) {
     const uint32_t nw = (a.n + 31) / 32;
     const uint32_t nq = (nw + 3) / 4;  // 16-byte quads per row
     const uint32_t nchunk = (nq + blockDim.x - 1) / blockDim.x;
@@ -216,7 +227,7 @@ __device__ __forceinline__ void bitmap_tile(const SelArgs& a, const uint32_t* li
     const uint32_t s0 = b * BM_BATCH, s1 = min(len, s0 + BM_BATCH);
     for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
         const uint32_t j = __ldcg(list + i);
-        if (j < a.T) s_off[atomicAdd(s_n, 1u)] = rec_off(a.recs[j]);
+        if (j < a.T && j >= a.j_lo && (!alive_only || __ldcg(alive_only + j))) s_off[atomicAdd(s_n, 1u)] = rec_off(a.recs[j]);
     }
     __syncthreads();
     const uint32_t rows = *s_n;
@@ -264,6 +275,33 @@ __global__ void __launch_bounds__(SEL_THREADS) bitmap_count_kernel(SelArgs a, co
     const uint32_t len = list_len_dev ? *list_len_dev : list_len_host;
     const uint64_t tiles = bitmap_tiles(a, len);
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) bitmap_tile(a, list, len, tile, sign, s_off, &s_n);
+}
+
+// Vertex-major tiles (Bitmax pools): cnt[v] += sum over the tiles of sets
+// [j_lo, T) of POPCOUNT(word v under the mask of those sets' columns).  One
+// thread owns four consecutive vertices, so no atomics are needed.
+__global__ void __launch_bounds__(SEL_THREADS) tile_count_kernel(SelArgs a, uint32_t j_lo) {
+    const uint32_t nq = (a.n + 3) / 4;
+    const uint32_t t0 = j_lo / 32, t1 = (a.T + 31) / 32;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        for (uint32_t t = t0; t < t1; t++) {
+            const uint32_t lo = max(j_lo, 32 * t), hi = min(a.T, 32 * t + 32);
+            const uint32_t cm = (hi - lo == 32) ? 0xFFFFFFFFu : (((1u << (hi - lo)) - 1u) << (lo - 32 * t));
+            const uint4 w = __ldg(reinterpret_cast<const uint4*>(a.bm_heap + (uint64_t)t * a.n4w) + q);
+            c0 += __popc(w.x & cm);
+            c1 += __popc(w.y & cm);
+            c2 += __popc(w.z & cm);
+            c3 += __popc(w.w & cm);
+        }
+        int4* c4 = reinterpret_cast<int4*>(a.cnt) + q;
+        int4 c = *c4;
+        c.x += (int)c0;
+        c.y += (int)c1;
+        c.z += (int)c2;
+        c.w += (int)c3;
+        *c4 = c;
+    }
 }
 
 // Uncompressed pools: one warp per set.
@@ -421,6 +459,75 @@ __device__ __forceinline__ uint32_t cover_warp(const SelArgs& a, uint32_t u, uin
         } else if (nit) {
             atomicMax(&a.st->pad, 2u);
         }
+    }
+    return member ? 1u : 0u;
+}
+
+// The persistent form's cover of sets [jb, jb + 32), one per lane (all lanes
+// call it): every alive set holding u is marked covered and its vertices lose
+// one count right away -- a covered Huffman set's chunks are spread over the
+// warp's lanes, a covered uncompressed set is walked by the whole warp --
+// while covered bitmap rows are listed for the bit-plane pass.  Returns the
+// lane's gain (0 or 1).
+__device__ __forceinline__ uint32_t cover_dec_warp(const SelArgs& a, const DecodeSmem& ds, uint32_t* hist,
+                                                   uint32_t hot, uint32_t u, uint32_t ru, uint32_t jb) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t j = jb + lane;
+    bool member = false;
+    uint32_t kind = KIND_PENDING, nit = 0, size = 0;
+    uint64_t off = 0;
+    if (j < a.T && __ldcg(a.alive + j)) {
+        const SetRec rec = a.recs[j];
+        kind = rec_kind(rec);
+        size = rec.size;
+        off = rec_off(rec);
+        nit = (rec.n_coded + 31) / 32 + (rec.size - rec.n_coded + 31) / 32;
+        if (kind == KIND_HUFF) {
+            const HuffView h = huff_view(a.code_heap, rec);
+            if (ru != NONE) member = huff_contains(a.cb, h, ru);
+            else member = sorted_contains(h.raw, h.n_raw, u);
+        } else if (kind == KIND_BITMAP) {
+            member = (__ldg(a.bm_heap + off + (u >> 5)) >> (u & 31)) & 1u;
+        } else {
+            const uint32_t* x = a.raw_heap + off;
+            for (uint32_t i = 0; i < rec.size && !member; i++) member = __ldg(x + i) == u;
+        }
+        if (member) a.alive[j] = 0;
+    }
+    // covered bitmap rows: one list append per warp
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, member && kind == KIND_BITMAP);
+    if (bal) {
+        const uint32_t leader = __ffs(bal) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&a.st->n_cov_bm, (uint32_t)__popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (member && kind == KIND_BITMAP) a.cov_bm[base + __popc(bal & lanemask_lt())] = j;
+    }
+    // covered Huffman sets: their chunks over the lanes
+    const uint32_t mine = (member && kind == KIND_HUFF) ? nit : 0u;
+    const uint32_t incl = warp_incl_scan(mine);
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t t = base + lane;
+        // owner lane of task t: the first lane whose inclusive count exceeds t
+        uint32_t lo = 0;
+#pragma unroll
+        for (uint32_t step = 16; step; step >>= 1) {
+            const uint32_t s = __shfl_sync(0xFFFFFFFFu, incl, lo + step - 1);
+            if (s <= t) lo += step;
+        }
+        const uint32_t oj = __shfl_sync(0xFFFFFFFFu, j, lo);
+        const uint32_t oex = __shfl_sync(0xFFFFFFFFu, incl - mine, lo);
+        count_chunk_warp(a, ds, hist, hot, t < total, oj, t - oex, -1);
+    }
+    // covered uncompressed sets: the warp walks each one
+    uint32_t rb = __ballot_sync(0xFFFFFFFFu, member && kind == KIND_RAW);
+    while (rb) {
+        const uint32_t l = __ffs(rb) - 1;
+        rb &= rb - 1;
+        const uint64_t o = __shfl_sync(0xFFFFFFFFu, off, l);
+        const uint32_t sz = __shfl_sync(0xFFFFFFFFu, size, l);
+        for (uint32_t q = lane; q < sz; q += 32) atomicAdd(&a.cnt[__ldg(a.raw_heap + o + q)], -1);
     }
     return member ? 1u : 0u;
 }
@@ -595,12 +702,57 @@ __global__ void __launch_bounds__(PS_THREADS) select_persistent_kernel(SelArgs a
             t_a += t - t_prev;
             t_prev = t;
         }
-        // ---- B: cover
+        // ---- B: cover (the persistent update form also decrements here)
         {
-            const uint32_t ru = a.has_cb ? __ldg(a.cb.rank_of + u) : NONE;
             uint32_t gain = 0;
-            for (uint32_t jb = (blockIdx.x * PS_THREADS + (threadIdx.x & ~31u)); jb < a.T; jb += nb * PS_THREADS)
-                gain += cover_warp(a, u, ru, jb);
+            if (a.tiles) {
+                // a tile's live columns holding u*: bits of word u* under the
+                // live mask; the tile and those columns go to the decrement list
+                const uint32_t ntiles = (a.T + 31) / 32;
+                for (uint32_t t = blockIdx.x * PS_THREADS + threadIdx.x; t < ntiles; t += nb * PS_THREADS) {
+                    const uint4* al = reinterpret_cast<const uint4*>(a.alive + 32ull * t);
+                    uint32_t am = 0;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const uint4 x = __ldcg(al + h);
+                        const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+#pragma unroll
+                            for (int b = 0; b < 4; b++)
+                                if ((xs[q] >> (8 * b)) & 0xFFu) am |= 1u << (16 * h + 4 * q + b);
+                    }
+                    const uint32_t hi = min(32u, a.T - 32 * t);
+                    if (hi < 32) am &= (1u << hi) - 1u;
+                    const uint32_t m = am & __ldg(a.bm_heap + (uint64_t)t * a.n4w + u);
+                    if (m) {
+                        for (uint32_t mm = m; mm; mm &= mm - 1) a.alive[32 * t + __ffs(mm) - 1] = 0;
+                        gain += __popc(m);
+                        const unsigned long long slot = atomicAdd(&a.st->n_dec, 1ull);
+                        if (slot < a.dec_cap) a.dec_items[slot] = ((unsigned long long)t << 32) | m;
+                        else atomicMax(&a.st->pad, 2u);
+                    }
+                    if (a.select_mode) a.tile_live[t] = am & ~m;
+                }
+            } else if (a.select_mode) {
+                const uint32_t ru = a.has_cb ? __ldg(a.cb.rank_of + u) : NONE;
+                for (uint32_t jb = (blockIdx.x * PS_THREADS + (threadIdx.x & ~31u)); jb < a.T; jb += nb * PS_THREADS)
+                    gain += cover_warp(a, u, ru, jb);
+                // recount: this iteration's counts are spent (u* is known)
+                for (uint32_t v = blockIdx.x * PS_THREADS + threadIdx.x; v < a.n; v += nb * PS_THREADS)
+                    if (__ldcg(a.cnt + v) > 0) a.cnt[v] = 0;
+            } else {
+                const uint32_t ru = a.has_cb ? __ldg(a.cb.rank_of + u) : NONE;
+                for (uint32_t i = threadIdx.x; i < hot; i += PS_THREADS) hist[i] = 0;
+                __syncthreads();
+                for (uint32_t jb = (blockIdx.x * PS_THREADS + (threadIdx.x & ~31u)); jb < a.T; jb += nb * PS_THREADS)
+                    gain += cover_dec_warp(a, ds, hist, hot, u, ru, jb);
+                __syncthreads();
+                for (uint32_t r = threadIdx.x; r < hot; r += PS_THREADS) {
+                    const uint32_t h = hist[r];
+                    if (h) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -(int)h);
+                }
+            }
             gain = warp_sum(gain);
             if (lane == 0 && gain) atomicAdd(&a.st->gain, (unsigned long long)gain);
         }
@@ -609,48 +761,82 @@ __global__ void __launch_bounds__(PS_THREADS) select_persistent_kernel(SelArgs a
             const unsigned long long t = globaltimer_ns();
             t_b += t - t_prev;
             t_prev = t;
+            // the iteration's gain is complete
+            const unsigned long long g = __ldcg(&a.st->gain);
+            a.marginal[it] = g;
+            a.st->covered += g;
+            a.st->it = it + 1;
         }
-        // ---- C: decrement
-        {
+        // ---- C: tiles (decrement or recount), recount, or the covered bitmap
+        // rows of the update form; skipped when none of these has work (every
+        // block reads the same counters after the barrier)
+        const uint32_t n_cov_bm = __ldcg(&a.st->n_cov_bm);
+        bool phase_c = true;
+        if (a.tiles) {
+            // one thread owns a vertex: cnt[v] -= POPCOUNT(word v & covered
+            // columns) over the covered tiles or, recounting, cnt[v] =
+            // POPCOUNT(word v & live columns) over every tile (Eq. (3))
+            const unsigned long long n_cov = min(__ldcg(&a.st->n_dec), a.dec_cap);
+            const uint32_t ntiles = (a.T + 31) / 32;
+            for (uint32_t v = blockIdx.x * PS_THREADS + threadIdx.x; v < a.n; v += nb * PS_THREADS) {
+                const int c = __ldcg(a.cnt + v);
+                if (c < 0) continue;
+                uint32_t acc = 0;
+                if (a.select_mode) {
+                    for (uint32_t t = 0; t < ntiles; t++)
+                        acc += __popc(__ldg(a.bm_heap + (uint64_t)t * a.n4w + v) & __ldcg(a.tile_live + t));
+                    a.cnt[v] = (int)acc;
+                } else {
+                    for (unsigned long long i = 0; i < n_cov; i++) {
+                        const unsigned long long item = __ldcg(a.dec_items + i);
+                        acc += __popc(__ldg(a.bm_heap + (item >> 32) * a.n4w + v) & (uint32_t)item);
+                    }
+                    if (acc) a.cnt[v] = c - (int)acc;
+                }
+            }
+            if (timer)
+                atomicAdd(&a.st->dec_bytes, 4ull * (a.select_mode ? (unsigned long long)ntiles : n_cov) * a.n4w);
+        } else if (a.select_mode) {
             for (uint32_t i = threadIdx.x; i < hot; i += PS_THREADS) hist[i] = 0;
             __syncthreads();
-            const unsigned long long n_dec = min(__ldcg(&a.st->n_dec), a.dec_cap);
+            // every chunk of the sets still live
             if (a.has_cb) {
                 const unsigned long long nwarps = (unsigned long long)nb * (PS_THREADS / 32);
                 for (unsigned long long wb = (unsigned long long)(blockIdx.x * (PS_THREADS / 32) + warp) * 32;
-                     wb < n_dec; wb += nwarps * 32)
-                    count_items_warp(a, ds, hist, hot, a.dec_items, n_dec, wb, -1);
+                     wb < a.n_items; wb += nwarps * 32)
+                    count_items_warp(a, ds, hist, hot, a.chunk_items, a.n_items, wb, 1, a.alive);
             }
             __syncthreads();
             for (uint32_t r = threadIdx.x; r < hot; r += PS_THREADS) {
                 const uint32_t h = hist[r];
-                if (h) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], -(int)h);
+                if (h) atomicAdd(&a.cnt[__ldg(a.cb.vertex_of_rank + r)], (int)h);
             }
-            const uint32_t n_bm = __ldcg(&a.st->n_cov_bm);
-            if (n_bm) {
-                const uint64_t tiles = bitmap_tiles(a, n_bm);
+            if (a.n_bm) {
+                const uint64_t tiles = bitmap_tiles(a, a.n_bm);
                 for (uint64_t tile = blockIdx.x; tile < tiles; tile += nb)
-                    bitmap_tile(a, a.cov_bm, n_bm, tile, -1, s_off, &s_n);
+                    bitmap_tile(a, a.bm_sets, a.n_bm, tile, 1, s_off, &s_n, a.alive);
             }
-            const uint32_t n_raw = __ldcg(&a.st->n_cov_raw);
-            for (uint32_t i = blockIdx.x * (PS_THREADS / 32) + warp; i < n_raw; i += nb * (PS_THREADS / 32)) {
-                const SetRec rec = a.recs[__ldcg(a.cov_raw + i)];
+            for (uint32_t j = blockIdx.x * (PS_THREADS / 32) + warp; j < a.T; j += nb * (PS_THREADS / 32)) {
+                const SetRec rec = a.recs[j];
+                if (rec_kind(rec) != KIND_RAW || !__ldcg(a.alive + j)) continue;
                 const uint32_t* x = a.raw_heap + rec_off(rec);
-                for (uint32_t q = lane; q < rec.size; q += 32) atomicAdd(&a.cnt[__ldg(x + q)], -1);
+                for (uint32_t q = lane; q < rec.size; q += 32) atomicAdd(&a.cnt[__ldg(x + q)], 1);
             }
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                const unsigned long long g = __ldcg(&a.st->gain);
-                a.marginal[it] = g;
-                a.st->covered += g;
-                a.st->it = it + 1;
-                if (n_bm) atomicAdd(&a.st->dec_bytes, 4ull * n_bm * (((a.n + 31) / 32 + 3) & ~3u));
-            }
+        } else if (n_cov_bm) {
+            const uint64_t tiles = bitmap_tiles(a, n_cov_bm);
+            for (uint64_t tile = blockIdx.x; tile < tiles; tile += nb)
+                bitmap_tile(a, a.cov_bm, n_cov_bm, tile, -1, s_off, &s_n);
+            if (timer) atomicAdd(&a.st->dec_bytes, 4ull * n_cov_bm * (((a.n + 31) / 32 + 3) & ~3u));
+        } else {
+            phase_c = false;
         }
-        if (!grid_barrier(bar, nb, a.wait_cycles, &s_ok)) return;
-        if (timer) {
-            const unsigned long long t = globaltimer_ns();
-            t_c += t - t_prev;
-            t_prev = t;
+        if (phase_c) {
+            if (!grid_barrier(bar, nb, a.wait_cycles, &s_ok)) return;
+            if (timer) {
+                const unsigned long long t = globaltimer_ns();
+                t_c += t - t_prev;
+                t_prev = t;
+            }
         }
         u_prev = u;
     }
@@ -717,6 +903,10 @@ cudaError_t launch_count(const SelArgs& a, uint32_t encode, cudaStream_t s) {
         count_items_kernel<<<sh.count_blocks, COUNT_THREADS, smem, s>>>(a, a.chunk_items, nullptr, a.n_items, 1);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+    }
+    if (a.tiles) {
+        tile_count_kernel<<<sh.count_blocks * 2, SEL_THREADS, 0, s>>>(a, a.j_lo);
+        return cudaGetLastError();
     }
     if (a.n_bm) {
         bitmap_count_kernel<<<sh.count_blocks * 2, SEL_THREADS, 0, s>>>(a, a.bm_sets, nullptr, a.n_bm, 1);
@@ -855,7 +1045,16 @@ __global__ void __launch_bounds__(SEL_THREADS) decode_kernel(DecodeArgs a) {
             uint32_t base = 0;
             for (uint32_t w0 = 0; w0 < nw; w0 += 32) {
                 const uint32_t w = w0 + lane;
-                uint32_t x = w < nw ? row[w] : 0u;
+                uint32_t x = 0;
+                if (a.tiles) {
+                    // column j % 32 of a vertex-major tile: vertex v is bit j % 32 of word v
+                    for (uint32_t b = 0; b < 32; b++) {
+                        const uint32_t v = w * 32 + b;
+                        if (v < a.n) x |= ((row[v] >> (j & 31)) & 1u) << b;
+                    }
+                } else if (w < nw) {
+                    x = row[w];
+                }
                 const uint32_t c = __popc(x);
                 const uint32_t incl = warp_incl_scan(c);
                 uint32_t p = base + incl - c;

@@ -5,7 +5,7 @@
 // at any time.  Worker threads (max_inflight of them) take the oldest queued
 // query whose pool is free and whose projected device footprint fits the memory
 // budget, and run IMM on it.  Pools are kept resident and keyed by (graph,
-// model, seed, epoch, encoding options): a later query on the same key reuses
+// model, seed, epoch, encoding options, scheme): a later query on the same key reuses
 // the sets already sampled (set j depends only on (seed, epoch, j)) and extends
 // them as needed.  Every pool has its own CUDA stream, so queries on different
 // pools overlap on the device.  Results equal hbx_imm's for the same arguments.
@@ -57,7 +57,7 @@ struct Query {
     std::string error;  // message of a failed query
 };
 
-using PoolKey = std::tuple<const hbx_graph*, int, uint64_t, uint32_t, uint32_t, uint32_t, uint32_t>;
+using PoolKey = std::tuple<const hbx_graph*, int, uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t>;
 
 struct PoolEntry {
     hbx_pool* pool = nullptr;
@@ -67,7 +67,8 @@ struct PoolEntry {
 };
 
 PoolKey key_of(const Query& q) {
-    return PoolKey(q.g, (int)q.model, q.seed, q.o.pool_epoch, q.o.encode, q.o.density_cut, q.o.warmup_sets);
+    return PoolKey(q.g, (int)q.model, q.seed, q.o.pool_epoch, q.o.encode, q.o.density_cut, q.o.warmup_sets,
+                   q.o.scheme);
 }
 
 }  // namespace

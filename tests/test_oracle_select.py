@@ -271,3 +271,54 @@ def test_scheme_switch_closed_forms():
     s2 = pool2.sizes(0, 400).astype(np.float64)
     assert abs(sk2 - stats.skew(s2, bias=True)) < 1e-9 * max(1.0, abs(sk2))
     assert bm2 == (sk2 < 0)
+
+
+def test_imm_fresh_final_phase():
+    """IMM with fresh final-phase sets: the estimation rounds and LB are those
+    of the reusing form, the final phase takes theta = ceil(lambda*/LB) new sets
+    (ids from T_i on), and greedy on exactly those sets gives the seeds."""
+    w = synth.WORKLOADS["ic_rmat4k"]
+    g = w.graph()
+    reuse = oracle.Pool(g, oracle.IC, w.rr_seed).imm(w.k, w.eps, w.ell)
+    pool = oracle.Pool(g, oracle.IC, w.rr_seed)
+    fresh = pool.imm(w.k, w.eps, w.ell, fresh_final=True)
+    prm = oracle.imm_params(g.n, w.k, w.eps, w.ell)
+    assert fresh["rounds"] == reuse["rounds"] and fresh["lb"] == reuse["lb"]
+    Ti = int(fresh["round_T"][fresh["rounds"] - 1])
+    theta = math.ceil(prm["lambda_star"] / fresh["lb"])
+    assert fresh["theta"] == theta and int(fresh["round_T"][fresh["rounds"]]) == Ti + theta
+    assert fresh["influence"] == g.n * fresh["covered"] / theta
+    # greedy over the fresh sets only (written out with the list greedy)
+    sets = [pool.set(j) for j in range(Ti, Ti + theta)]
+    s2, m2, c2 = oracle.greedy_lists(g.n, sets, w.k)
+    assert s2.tolist() == fresh["seeds"].tolist() and m2.tolist() == fresh["marginal"].tolist()
+    assert c2 == fresh["covered"]
+
+
+def test_imm_fresh_estimate_close_to_brute_force_sigma():
+    n = 8
+    edges = [(0, 1), (0, 2), (1, 3), (2, 3), (3, 4), (4, 5), (5, 6), (6, 7), (7, 0), (2, 6), (1, 5), (3, 7)]
+    probs = np.array([0.7, 0.6, 0.5, 0.4, 0.8, 0.3, 0.6, 0.5, 0.2, 0.4, 0.3, 0.5], dtype=np.float32)
+    g = synth.from_edges(n, edges, prob=probs)
+    r = oracle.Pool(g, oracle.IC, 5).imm(2, 0.3, 1.0, fresh_final=True)
+    S = r["seeds"].tolist()
+    p_exact = [np.ceil(float(p) * 2**24) / 2**24 for p in probs]
+    sigma = 0.0
+    for mask in range(1 << len(edges)):
+        pr = 1.0
+        out = [[] for _ in range(n)]
+        for i, (u, v) in enumerate(edges):
+            if mask >> i & 1:
+                pr *= p_exact[i]
+                out[u].append(v)
+            else:
+                pr *= 1 - p_exact[i]
+        seen, stack = set(S), list(S)
+        while stack:
+            u = stack.pop()
+            for v in out[u]:
+                if v not in seen:
+                    seen.add(v)
+                    stack.append(v)
+        sigma += pr * len(seen)
+    assert abs(r["influence"] - sigma) <= 0.3 * sigma
