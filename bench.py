@@ -491,22 +491,11 @@ def run_hbx(args, rank, world, local_rank):
         return args.budget_s - (time.perf_counter() - t_start)
 
     skipped = {}
-    secondary = None
-    if args.secondary and world == 1:
-        if left() > 120:
-            secondary = secondary_leg(hbx, synth, tc, args.secondary, 12, 3, flush, peak, peak_kind,
-                                      not args.no_cpu_baseline)
-        else:
-            skipped["secondary"] = "time budget"
-    serving = None
-    if args.serving:
-        if left() > 240:
-            serving = serving_leg(hbx, synth, tc, args.serving)
-        else:
-            skipped["serving"] = "time budget"
+    # the oracle baseline first (the contract's), then the optional legs in
+    # order of importance, each only if its estimate fits the time budget
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        if left() > 200:
+        if left() > 150:
             cpu = oracle_baseline(g, w)
         else:
             skipped["cpu_baseline"] = "time budget"
@@ -514,11 +503,24 @@ def run_hbx(args, rank, world, local_rank):
     if not args.no_plain and args.form == 1:
         enc = args.plain_encode if args.plain_encode >= 0 else (1 if w.name in INT32_TOO_BIG else 0)
         pw = args.plain_warmup if args.plain_warmup >= 0 else (0 if w.name in INT32_TOO_BIG else 1)
-        # the plain form ran about 5x slower than the batched one at full size
-        if left() > 10 * imm_ms / 1000.0 * (args.plain_steps + pw) + 30:
+        # the plain form ran 5-7x slower than the batched one at full size
+        if left() > 7 * imm_ms / 1000.0 * (args.plain_steps + pw) + 30:
             plain = plain_leg(hbx, tc, G, w, seed, args.plain_steps, pw, enc, flush, imm_ms, r)
         else:
             skipped["plain_form"] = "time budget"
+    secondary = None
+    if args.secondary and world == 1:
+        if left() > 90:
+            secondary = secondary_leg(hbx, synth, tc, args.secondary, 12, 3, flush, peak, peak_kind,
+                                      not args.no_cpu_baseline)
+        else:
+            skipped["secondary"] = "time budget"
+    serving = None
+    if args.serving:
+        if left() > 180:
+            serving = serving_leg(hbx, synth, tc, args.serving)
+        else:
+            skipped["serving"] = "time budget"
 
     s0 = stats[-1]
     search = search_roofline(stats, ceiling)

@@ -177,8 +177,13 @@ typedef struct {
      * (the per-graph scheme), 3 Bitmax in vertex-major tiles; and the warm-up
      * sizes' skewness that the per-graph scheme decided on */
     uint32_t scheme;
-    uint32_t reserved;
+    /* launch shape: capacity of the second warp tier that takes the sets
+     * outgrowing warp_capacity before the block tiers (0: none) */
+    uint32_t second_warp_capacity;
     double scheme_skewness;
+    /* batched form: time of the selections' argmax phases (barrier to
+     * barrier, as dec_s) */
+    double argmax_s;
 } hbx_stats;
 
 /* Human-readable name of an HBX_ERR_* code. */

@@ -41,6 +41,10 @@ constexpr int MS_WARPS = MS_THREADS / 32;
 // MS_CHUNK groups, one warp per chunk.
 constexpr uint32_t MS_HEAVY = 32;
 constexpr uint32_t MS_CHUNK = 256;
+// A group's sources' visited masks are read only when at least this many sets
+// hold its vertex in their frontier: for fewer, the gathers (which mostly miss
+// L2 on the largest graphs) cost more than the Philox blocks they save.
+constexpr uint32_t MS_VIS_MIN = 4;
 
 // Per-warp live-edge counts of the batch's sets in shared memory, added to the
 // batch totals when the warp is done.
@@ -110,7 +114,13 @@ __device__ __forceinline__ MsGroup ms_stage(const MsArgs& a, bool valid, uint32_
 
 __device__ __forceinline__ void ms_visited(const MsArgs& a, MsGroup& G, bool valid, uint32_t gg, uint32_t eb,
                                            uint32_t ee, uint32_t f) {
-    if (valid && f) {
+    if (valid && f && (uint32_t)__popc(f) < MS_VIS_MIN) {
+        const uint32_t e0 = gg * 4u;
+        if (e0 >= eb && e0 < ee) G.um.x = f;
+        if (e0 + 1 >= eb && e0 + 1 < ee) G.um.y = f;
+        if (e0 + 2 >= eb && e0 + 2 < ee) G.um.z = f;
+        if (e0 + 3 >= eb && e0 + 3 < ee) G.um.w = f;
+    } else if (valid && f) {
         const uint32_t e0 = gg * 4u;
         if (e0 >= eb && e0 < ee) G.um.x = f & ~__ldg(a.vis + G.c.x);
         if (e0 + 1 >= eb && e0 + 1 < ee) G.um.y = f & ~__ldg(a.vis + G.c.y);
@@ -164,35 +174,54 @@ __device__ __forceinline__ void ms_round(const MsArgs& a, MsRound& R, const uint
         }
     }
     __syncwarp();
-    for (uint32_t t = lane; t < total; t += 32) {
-        uint32_t slot, s;
-        if (t < MS_ITEMS) {
-            const uint32_t it = R.items[t];
-            slot = it >> 5;
-            s = it & 31u;
-        } else {
-            // past the list: slot = number of slots whose inclusive count is <= t
-            slot = 0;
+    // two pairs per lane per step: their Philox blocks are independent, so the
+    // rounds of one fill the other's multiply latency
+    for (uint32_t t0 = lane; t0 < total; t0 += 64) {
+        uint32_t slot[2], s[2];
+        bool have[2];
 #pragma unroll
-            for (uint32_t step = MS_ROUND / 2; step; step >>= 1)
-                if (R.scan[slot + step - 1] <= t) slot += step;
-            const uint32_t nd = R.need[slot];
-            s = nth_set_bit(nd, t - (R.scan[slot] - (uint32_t)__popc(nd)));
+        for (int q = 0; q < 2; q++) {
+            const uint32_t t = t0 + 32 * q;
+            have[q] = t < total;
+            slot[q] = 0;
+            s[q] = 0;
+            if (!have[q]) continue;
+            if (t < MS_ITEMS) {
+                const uint32_t it = R.items[t];
+                slot[q] = it >> 5;
+                s[q] = it & 31u;
+            } else {
+                // past the list: slot = number of slots whose inclusive count is <= t
+                uint32_t sl = 0;
+#pragma unroll
+                for (uint32_t step = MS_ROUND / 2; step; step >>= 1)
+                    if (R.scan[sl + step - 1] <= t) sl += step;
+                const uint32_t nd = R.need[sl];
+                slot[q] = sl;
+                s[q] = nth_set_bit(nd, t - (R.scan[sl] - (uint32_t)__popc(nd)));
+            }
         }
-        const uint4 x = philox4x32_10_rk(make_uint4(R.gg[slot], s_sets[s], a.epoch, STREAM_IC), a.rk);
-        const uint4 th = R.thr[slot], u = R.um[slot];
-        const uint32_t bit = 1u << s;
-        const bool l0 = (u.x & bit) && ic_live(x.x, th.x);
-        const bool l1 = (u.y & bit) && ic_live(x.y, th.y);
-        const bool l2 = (u.z & bit) && ic_live(x.z, th.z);
-        const bool l3 = (u.w & bit) && ic_live(x.w, th.w);
-        if (l0 | l1 | l2 | l3) {
-            uint32_t* em = reinterpret_cast<uint32_t*>(&R.em[slot]);
-            if (l0) atomicOr(em + 0, bit);
-            if (l1) atomicOr(em + 1, bit);
-            if (l2) atomicOr(em + 2, bit);
-            if (l3) atomicOr(em + 3, bit);
-            atomicAdd(&s_live_w[s], (uint32_t)l0 + (uint32_t)l1 + (uint32_t)l2 + (uint32_t)l3);
+        uint4 x[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+            x[q] = philox4x32_10_rk(make_uint4(R.gg[slot[q]], s_sets[s[q]], a.epoch, STREAM_IC), a.rk);
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            if (!have[q]) continue;
+            const uint4 th = R.thr[slot[q]], u = R.um[slot[q]];
+            const uint32_t bit = 1u << s[q];
+            const bool l0 = (u.x & bit) && ic_live(x[q].x, th.x);
+            const bool l1 = (u.y & bit) && ic_live(x[q].y, th.y);
+            const bool l2 = (u.z & bit) && ic_live(x[q].z, th.z);
+            const bool l3 = (u.w & bit) && ic_live(x[q].w, th.w);
+            if (l0 | l1 | l2 | l3) {
+                uint32_t* em = reinterpret_cast<uint32_t*>(&R.em[slot[q]]);
+                if (l0) atomicOr(em + 0, bit);
+                if (l1) atomicOr(em + 1, bit);
+                if (l2) atomicOr(em + 2, bit);
+                if (l3) atomicOr(em + 3, bit);
+                atomicAdd(&s_live_w[s[q]], (uint32_t)l0 + (uint32_t)l1 + (uint32_t)l2 + (uint32_t)l3);
+            }
         }
     }
     __syncwarp();

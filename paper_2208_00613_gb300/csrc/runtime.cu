@@ -715,7 +715,19 @@ static int run_sample(hbx_pool* p, uint32_t mode, uint32_t j0, uint32_t count, c
             RC(run_block_path(p, a, count, 1u, timed));
         } else {
             RC(timed_launch(p, timed, [&] { return launch_sample_warp(a, sh.qw, ctx->sms, p->stream); }));
-            const uint32_t nmid = (uint32_t)p->hc.big_count;
+            uint32_t nmid = (uint32_t)p->hc.big_count;
+            if (nmid && sh.q2) {
+                // the sets that outgrew the warp go through warps of capacity q2
+                // first (many more of them in flight than shared-memory blocks;
+                // thin deep sets gain most), then on to the block tiers
+                CK(cudaMemcpyAsync(p->list_in, p->big_list, (size_t)nmid * 4, cudaMemcpyDeviceToDevice, p->stream));
+                CK(cudaMemsetAsync(p->ctr, 0, sizeof(unsigned long long), p->stream));  // work
+                CK(cudaMemsetAsync(&p->ctr->big_count, 0, sizeof(unsigned long long), p->stream));
+                SampleArgs a2 = sample_args(p, mode, 0, nmid, p->list_in, freq, cut, sh);
+                a2.group_budget = 0xFFFFFFFFu;
+                RC(timed_launch(p, timed, [&] { return launch_sample_warp(a2, sh.q2, ctx->sms, p->stream); }));
+                nmid = (uint32_t)p->hc.big_count;
+            }
             if (nmid) RC(timed_launch(p, timed, [&] { return launch_sample_mid(a, nmid, ctx->sms, p->stream); }));
             uint32_t nbig = (uint32_t)p->hc.giant_count;
             if (nbig && p->model == HBX_IC && mode != MODE_RAW) {
@@ -898,13 +910,14 @@ static int build_codebook(hbx_pool* p, const std::vector<uint32_t>& freq) {
 static int choose_shape(hbx_pool* p, Shape* out) {
     hbx_ctx* ctx = p->ctx;
     if (!p->o.form) {  // the plain form runs the block kernel only
-        *out = {256, 2048, 1};
+        *out = {256, 2048, 1, 0};
         return HBX_OK;
     }
     if (p->o.warp_capacity) {
         out->qw = p->o.warp_capacity;
         out->gb = p->o.warp_group_budget ? p->o.warp_group_budget : 2048u;
         out->bc = p->o.block_cluster ? p->o.block_cluster : 1u;
+        out->q2 = 0;
         return HBX_OK;
     }
     auto key = std::make_pair(p->g->fingerprint, (int)p->model);
@@ -916,15 +929,17 @@ static int choose_shape(hbx_pool* p, Shape* out) {
             return HBX_OK;
         }
     }
-    const Shape cands[] = {{64, 0, 1},      {128, 256, 1},  {128, 1024, 1}, {256, 4096, 1},
-                           {128, 1024, 2},  {256, 1024, 2}, {256, 4096, 4}, {512, 4096, 1}};
+    // (warp capacity, warp group budget, cluster size, second warp tier)
+    const Shape cands[] = {{64, 0, 1, 0},       {128, 256, 1, 0},    {128, 1024, 1, 0},  {256, 4096, 1, 0},
+                           {128, 1024, 2, 0},   {256, 1024, 2, 0},   {256, 4096, 4, 0},  {512, 4096, 1, 0},
+                           {128, 1024, 1, 1024}, {128, 256, 1, 2048}, {256, 4096, 1, 1024}};
     uint32_t* freq = nullptr;
     RC(grow_buffer(p, (void**)&freq, 0, (size_t)p->g->n * 4, 0));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    Shape best = {256, 2048, 1};
+    Shape best = {256, 2048, 1, 0};
     const uint32_t base = 0x40000000u;  // calibration ids, never part of a pool prefix
     const unsigned long long sc0 = p->hc.edges_scanned, lv0 = p->hc.edges_live;
     // Calibration batch: 8192 sets timed twice per shape, or, where a probe of
@@ -1384,6 +1399,7 @@ static int pool_select_finish(hbx_pool* p, uint32_t k, uint32_t* seeds, uint64_t
     p->select_iterations += hs.it;
     p->dec_bytes += hs.dec_bytes;
     p->dec_s += 1e-9 * (double)(hs.t_cover_ns + hs.t_dec_ns);
+    p->argmax_s += 1e-9 * (double)hs.t_argmax_ns;
     if (hs.pad == 1) return fail(ctx, HBX_ERR_INTERNAL, "undecodable Huffman stream during selection");
     if (hs.pad) return fail(ctx, HBX_ERR_INTERNAL, "decrement item list overflow during selection");
     if (hs.it != k) return fail(ctx, HBX_ERR_INTERNAL, "selection ran " + std::to_string(hs.it) + " iterations");
@@ -1558,6 +1574,7 @@ void fill_stats(hbx_pool* p, hbx_stats* s) {
     s->warp_capacity = p->shape.qw;
     s->warp_group_budget = p->shape.gb;
     s->block_cluster = p->shape.bc;
+    s->second_warp_capacity = p->shape.q2;
     double mom[3] = {0, 0, 0};
     cudaMemcpyAsync(mom, p->moments, 3 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
     cudaStreamSynchronize(p->stream);
@@ -1588,6 +1605,7 @@ void fill_stats(hbx_pool* p, hbx_stats* s) {
     s->uncoded_vertices = p->hc.uncoded;
     s->scheme = !p->o.scheme ? 0u : (!p->bitmax ? 1u : (p->tiles ? 3u : 2u));
     s->scheme_skewness = p->scheme_skew;
+    s->argmax_s = p->argmax_s;
 }
 
 int imm_on_pool(hbx_pool* p, uint32_t k, double eps, double ell, uint32_t* seeds, double* influence,

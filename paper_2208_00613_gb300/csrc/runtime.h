@@ -22,6 +22,7 @@ struct Shape {
     uint32_t qw;
     uint32_t gb;
     uint32_t bc;  // blocks per cluster working on one heavy set
+    uint32_t q2;  // capacity of a second warp tier for the sets that outgrow qw (0: none)
 };
 struct Heap {
     uint32_t* d = nullptr;
@@ -127,7 +128,7 @@ struct hbx_pool {
     double count_kernel_s = 0;
     uint64_t count_bytes = 0;
     cudaEvent_t evc0 = nullptr, evc1 = nullptr, evs0 = nullptr, evs1 = nullptr;
-    double select_kernel_s = 0, dec_s = 0;
+    double select_kernel_s = 0, dec_s = 0, argmax_s = 0;
     uint64_t select_iterations = 0, dec_bytes = 0;
     double ms_kernel_s = 0;
     uint64_t ms_nsets = 0, ms_blocks = 0;

@@ -327,6 +327,12 @@ def test_imm_wc_1m(ctx):
     assert r["seeds"].tolist() == ro["seeds"].tolist()
     assert r["marginal"].tolist() == ro["marginal"].tolist()
     assert r["influence"] == ro["influence"]
+    # the warm-up block is ceil(T_1 / 8) sets, T_1 being IMM's first sampling
+    # target (the reading of Algorithm 1's "first block" when theta is not
+    # known up front); its copy-array share is reported
+    T1 = int(ro["round_T"][0])
+    assert r["stats"]["warmup_sets"] == (T1 + 7) // 8
+    assert 0 < r["stats"]["uncoded_vertices"] < r["stats"]["rr_vertices"]
     hbx.hbx_graph_destroy(G)
 
 
