@@ -184,6 +184,11 @@ typedef struct {
     /* batched form: time of the selections' argmax phases (barrier to
      * barrier, as dec_s) */
     double argmax_s;
+    /* the bit-parallel search: edge groups staged (one per in-edge group of a
+     * frontier vertex per level, for all the sets that expand it then), and
+     * vertex expansions deferred by a level so that more sets share one */
+    uint64_t ms_group_visits;
+    uint64_t ms_deferrals;
 } hbx_stats;
 
 /* Human-readable name of an HBX_ERR_* code. */

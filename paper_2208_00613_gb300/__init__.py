@@ -56,7 +56,7 @@ class hbx_stats(ctypes.Structure):
                 ("select_kernel_s", ctypes.c_double), ("select_iterations", ctypes.c_uint64),
                 ("dec_s", ctypes.c_double), ("dec_bytes", ctypes.c_uint64), ("uncoded_vertices", ctypes.c_uint64),
                 ("scheme", ctypes.c_uint32), ("second_warp_capacity", ctypes.c_uint32), ("scheme_skewness", ctypes.c_double),
-                ("argmax_s", ctypes.c_double)]
+                ("argmax_s", ctypes.c_double), ("ms_group_visits", ctypes.c_uint64), ("ms_deferrals", ctypes.c_uint64)]
 
     def to_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

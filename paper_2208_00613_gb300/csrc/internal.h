@@ -20,10 +20,14 @@ constexpr uint32_t MS_SETS = 32;  // sets searched together, one mask bit each
 struct MsCounters {
     uint32_t nF, nN, nH, nsets;       // frontier, next frontier being compacted, heavy chunks of this level;
                                       // sets of the batch
+    uint32_t npend;                   // vertices whose expansion the compaction being run deferred
+    uint32_t force;                   // this level's compaction expands every deferred vertex
     unsigned long long size[MS_SETS];     // per set of the batch
     unsigned long long scanned[MS_SETS];
     unsigned long long live[MS_SETS];
     unsigned long long blocks;  // Philox blocks drawn for the batch
+    unsigned long long visits;  // edge groups staged (one per group of a frontier vertex per level)
+    unsigned long long deferred;  // vertex expansions deferred by a level
 };
 
 struct MsArgs {
@@ -36,6 +40,10 @@ struct MsArgs {
     uint32_t* nxt;         // [n] masks: reached during this level
     uint32_t* F;           // [n] frontier vertices
     uint32_t* Ff;          // [n] their masks: the sets whose frontier holds them
+    uint32_t* pend;        // [n] sets whose expansion of the vertex is deferred (valid where ndef != 0)
+    uint32_t* ndef;        // [n/4] one byte per vertex: levels its expansion has been deferred (0: none pending)
+    uint32_t defer_groups; // vertices of more edge groups than this may have their expansion deferred
+    uint32_t defer_max;    // by at most this many levels (0: never)
     uint4* heavy;          // (vertex, first group, end group, mask) chunks of this level's heavy vertices
     uint32_t heavy_cap;
     MsCounters* mc;
@@ -53,6 +61,10 @@ cudaError_t launch_ms_start(const MsArgs& a, int sms, cudaStream_t s);
 // levels can be captured in a CUDA graph)
 cudaError_t launch_ms_level(const MsArgs& a, int sms, cudaStream_t s);
 constexpr int MS_GRAPH_LEVELS = 8;  // levels per graph launch
+// Expansion of a vertex of more than MS_DEFER_GROUPS edge groups (512 in-edges)
+// may wait up to MS_DEFER_MAX levels for more sets to reach it.
+constexpr uint32_t MS_DEFER_GROUPS = 128;
+constexpr uint32_t MS_DEFER_MAX = 2;
 // per-set sizes and scanned edges into a.mc
 cudaError_t launch_ms_finish(const MsArgs& a, int sms, cudaStream_t s);
 // bitmap rows and records of the dense sets; masks cleared

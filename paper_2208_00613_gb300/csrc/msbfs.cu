@@ -55,12 +55,14 @@ __device__ __forceinline__ void ms_init_shared(const MsArgs& a, uint32_t* s_sets
     __syncthreads();
 }
 
-__device__ __forceinline__ void ms_flush_live(const MsArgs& a, uint32_t (*s_live)[MS_SETS], uint32_t nblk) {
+__device__ __forceinline__ void ms_flush_live(const MsArgs& a, uint32_t (*s_live)[MS_SETS], uint32_t nblk,
+                                              uint32_t nvis) {
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncwarp();
     const uint32_t c = s_live[warp][lane];
     if (c) atomicAdd(&a.mc->live[lane], (unsigned long long)c);
     if (lane == 0 && nblk) atomicAdd(&a.mc->blocks, (unsigned long long)nblk);
+    if (lane == 0 && nvis) atomicAdd(&a.mc->visits, (unsigned long long)nvis);
 }
 
 // One warp's staging of a round: up to MS_ROUND aligned groups of 4 in-edges,
@@ -140,13 +142,14 @@ __device__ __forceinline__ void ms_visited(const MsArgs& a, MsGroup& G, bool val
 // collected per edge in shared memory and then ORed into nxt[source] with one
 // reduction per edge.
 __device__ __forceinline__ void ms_round(const MsArgs& a, MsRound& R, const uint32_t* s_sets, uint32_t* s_live_w,
-                                         uint32_t& nblk, const bool* valid, const uint32_t* gg,
+                                         uint32_t& nblk, uint32_t& nvis, const bool* valid, const uint32_t* gg,
                                          const uint32_t* eb, const uint32_t* ee, const uint32_t* f) {
     const uint32_t lane = threadIdx.x & 31;
     MsGroup G0 = ms_stage(a, valid[0], gg[0], eb[0], ee[0], f[0]);
     MsGroup G1 = ms_stage(a, valid[1], gg[1], eb[1], ee[1], f[1]);
     ms_visited(a, G0, valid[0], gg[0], eb[0], ee[0], f[0]);
     ms_visited(a, G1, valid[1], gg[1], eb[1], ee[1], f[1]);
+    nvis += __popc(__ballot_sync(0xFFFFFFFFu, valid[0] && f[0])) + __popc(__ballot_sync(0xFFFFFFFFu, valid[1] && f[1]));
     const uint32_t n0 = __popc(G0.need), n1 = __popc(G1.need);
     const uint32_t incl = warp_incl_scan(n0 + n1);
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
     ms_init_shared(a, s_sets, s_live);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * MS_WARPS * 32;
-    uint32_t nblk = 0;
+    uint32_t nblk = 0, nvis = 0;
     for (uint32_t c = (blockIdx.x * MS_WARPS + warp) * 32; c < nF; c += stride) {
         const uint32_t i = c + lane;
         uint32_t v = 0, f = 0, b = 0, e = 0, gfirst = 0, ng = 0;
@@ -310,11 +313,11 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
                     ff[k] = w_f[warp][lo];
                 }
             }
-            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, ok, gg, eb, ee, ff);
+            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, nvis, ok, gg, eb, ee, ff);
         }
         __syncwarp();
     }
-    ms_flush_live(a, s_live, nblk);
+    ms_flush_live(a, s_live, nblk, nvis);
 }
 
 __global__ void __launch_bounds__(MS_THREADS, 4) ms_heavy_kernel(MsArgs a) {
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_heavy_kernel(MsArgs a) {
     if (blockIdx.x * MS_WARPS >= nH) return;
     ms_init_shared(a, s_sets, s_live);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t nblk = 0;
+    uint32_t nblk = 0, nvis = 0;
     for (uint32_t it = blockIdx.x * MS_WARPS + warp; it < nH; it += gridDim.x * MS_WARPS) {
         const uint4 item = a.heavy[it];  // one chunk per warp
         const uint32_t eb = __ldg(a.g.row_ptr + item.x), ee = __ldg(a.g.row_ptr + item.x + 1);
@@ -333,42 +336,83 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_heavy_kernel(MsArgs a) {
             const bool ok[2] = {g + lane < item.z, g + 32 + lane < item.z};
             const uint32_t gg[2] = {g + lane, g + 32 + lane}, ebs[2] = {eb, eb}, ees[2] = {ee, ee};
             const uint32_t ff[2] = {item.w, item.w};
-            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, ok, gg, ebs, ees, ff);
+            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, nvis, ok, gg, ebs, ees, ff);
         }
     }
-    ms_flush_live(a, s_live, nblk);
+    ms_flush_live(a, s_live, nblk, nvis);
 }
 
 // The vertices reached during the level, with the sets that had not visited
-// them yet, become the next frontier (warp-aggregated appends); vis gains
-// those sets and nxt is cleared.  A thread takes 4 vertices with 16-byte
-// loads (the mask arrays are padded to a multiple of 4 entries).
+// them yet, join the next frontier (warp-aggregated appends); vis gains those
+// sets and nxt is cleared.  A vertex of more than defer_groups edge groups may
+// instead wait: its sets are kept in pend and it is reconsidered at the next
+// compaction, at most defer_max times in a row, so that sets reaching it at
+// nearby levels share one pass over its in-edges (and by then more of its
+// sources are visited, so fewer coins are drawn).  The sets do not depend on
+// when a member's in-edges are expanded.  When a level's frontier would be
+// empty with vertices still waiting, the next compaction (force) takes them
+// all.  A thread takes 4 vertices with 16-byte loads (the mask arrays are
+// padded to a multiple of 4 entries; ndef holds one byte per vertex).
 __global__ void __launch_bounds__(MS_THREADS) ms_compact_kernel(MsArgs a, bool after_level) {
-    if (after_level && a.mc->nF == 0) return;  // the search has ended: nxt is clear
+    const bool force = a.mc->force != 0;
+    if (after_level && a.mc->nF == 0 && !force) return;  // the search has ended: nxt is clear
     const uint32_t lane = threadIdx.x & 31, n4 = (a.g.n + 3) / 4;
     const uint32_t stride = gridDim.x * MS_THREADS;
     uint4* nxt4 = reinterpret_cast<uint4*>(a.nxt);
     uint4* vis4 = reinterpret_cast<uint4*>(a.vis);
+    const uint4* pend4 = reinterpret_cast<const uint4*>(a.pend);
+    uint32_t npend = 0;
     for (uint32_t q0 = blockIdx.x * MS_THREADS + (threadIdx.x & ~31u); q0 < n4; q0 += stride) {
         const uint32_t q = q0 + lane;
-        uint4 f = make_uint4(0, 0, 0, 0);
+        uint32_t fw[4] = {0, 0, 0, 0};
         if (q < n4) {
             const uint4 x = nxt4[q];
+            const uint32_t nd = a.ndef[q];
             if (x.x | x.y | x.z | x.w) {
                 nxt4[q] = make_uint4(0, 0, 0, 0);
                 const uint4 old = vis4[q];
-                f = make_uint4(x.x & ~old.x, x.y & ~old.y, x.z & ~old.z, x.w & ~old.w);
+                const uint4 f = make_uint4(x.x & ~old.x, x.y & ~old.y, x.z & ~old.z, x.w & ~old.w);
                 if (f.x | f.y | f.z | f.w) vis4[q] = make_uint4(old.x | f.x, old.y | f.y, old.z | f.z, old.w | f.w);
+                fw[0] = f.x;
+                fw[1] = f.y;
+                fw[2] = f.z;
+                fw[3] = f.w;
+            }
+            if (nd) {
+                const uint4 pd = pend4[q];
+                const uint32_t pw[4] = {pd.x, pd.y, pd.z, pd.w};
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if ((nd >> (8 * k)) & 0xFFu) fw[k] |= pw[k];
+            }
+            if ((fw[0] | fw[1] | fw[2] | fw[3]) && a.defer_max && !force) {
+                uint32_t nd2 = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (!fw[k]) continue;
+                    const uint32_t v = q * 4 + k;
+                    const uint32_t b = __ldg(a.g.row_ptr + v), e = __ldg(a.g.row_ptr + v + 1);
+                    const uint32_t ng = e > b ? ((e - 1) >> 2) - (b >> 2) + 1 : 0u;
+                    const uint32_t d = (nd >> (8 * k)) & 0xFFu;
+                    if (ng > a.defer_groups && d < a.defer_max) {
+                        a.pend[v] = fw[k];
+                        nd2 |= (d + 1) << (8 * k);
+                        fw[k] = 0;
+                        npend++;
+                    }
+                }
+                if (nd2 != nd) a.ndef[q] = nd2;
+            } else if (nd) {
+                a.ndef[q] = 0;
             }
         }
-        const uint32_t c = (f.x != 0) + (f.y != 0) + (f.z != 0) + (f.w != 0);
+        const uint32_t c = (fw[0] != 0) + (fw[1] != 0) + (fw[2] != 0) + (fw[3] != 0);
         const uint32_t incl = warp_incl_scan(c);
         const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         if (!total) continue;
         uint32_t pos = 0;
         if (lane == 31) pos = atomicAdd(&a.mc->nN, total);
         pos = __shfl_sync(0xFFFFFFFFu, pos, 31) + incl - c;
-        const uint32_t fw[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
         for (int k = 0; k < 4; k++)
             if (fw[k]) {
@@ -377,14 +421,23 @@ __global__ void __launch_bounds__(MS_THREADS) ms_compact_kernel(MsArgs a, bool a
                 pos++;
             }
     }
+    npend = __reduce_add_sync(0xFFFFFFFFu, npend);
+    if (lane == 0 && npend) {
+        atomicAdd(&a.mc->npend, npend);
+        atomicAdd(&a.mc->deferred, (unsigned long long)npend);
+    }
 }
 
-// Next level: the compacted list becomes the frontier.  <<<1, 1>>>
+// Next level: the compacted list becomes the frontier; if it is empty while
+// vertices wait, the next compaction takes them all.  <<<1, 1>>>
 __global__ void ms_advance_kernel(MsArgs a) {
-    if (a.mc->nF == 0 && a.mc->nN == 0) return;
-    a.mc->nF = a.mc->nN;
-    a.mc->nN = 0;
-    a.mc->nH = 0;
+    MsCounters* c = a.mc;
+    if (c->nF == 0 && c->nN == 0 && c->npend == 0 && !c->force) return;
+    c->force = (c->nN == 0 && c->npend > 0) ? 1u : 0u;
+    c->nF = c->nN;
+    c->nN = 0;
+    c->nH = 0;
+    c->npend = 0;
 }
 
 // Size and scanned in-edges of each set of the batch, from the visited masks:

@@ -542,6 +542,8 @@ static int ensure_ms_scratch(hbx_pool* p) {
     RC(grow_buffer(p, (void**)&p->ms_nxt, 0, n4, 0));
     RC(grow_buffer(p, (void**)&p->ms_F, 0, n4, 0));
     RC(grow_buffer(p, (void**)&p->ms_N, 0, n4, 0));
+    RC(grow_buffer(p, (void**)&p->ms_pend, 0, n4, 0));
+    RC(grow_buffer(p, (void**)&p->ms_ndef, 0, n4 / 4, 0));  // zero: nothing deferred
     // a heavy vertex has more than 32 edge groups, so at most m/128 of them,
     // each cut into chunks of 256 groups
     const uint64_t m = p->g->m;
@@ -568,6 +570,10 @@ static MsArgs ms_args(hbx_pool* p) {
     a.nxt = p->ms_nxt;
     a.F = p->ms_F;
     a.Ff = p->ms_N;
+    a.pend = p->ms_pend;
+    a.ndef = p->ms_ndef;
+    a.defer_groups = MS_DEFER_GROUPS;
+    a.defer_max = MS_DEFER_MAX;
     a.heavy = p->ms_heavy;
     a.heavy_cap = p->ms_heavy_cap;
     a.mc = p->ms_c;
@@ -620,10 +626,11 @@ static int ms_search_batch(hbx_pool* p, const uint32_t* ids, uint32_t nb, bool t
         if (level > (uint64_t)n) return fail(ctx, HBX_ERR_INTERNAL, "bit-parallel search did not end");
         CK(cudaGraphLaunch(level ? p->ms_more : p->ms_first, p->stream));
         p->launches += (level ? 0 : 3) + 4 * MS_GRAPH_LEVELS;
-        uint32_t nF = 0;
-        CK(cudaMemcpyAsync(&nF, &p->ms_c->nF, 4, cudaMemcpyDeviceToHost, p->stream));
+        // the first six words: frontier sizes, set count, deferred vertices, force
+        uint32_t head[6] = {0};
+        CK(cudaMemcpyAsync(head, p->ms_c, sizeof(head), cudaMemcpyDeviceToHost, p->stream));
         CK(cudaStreamSynchronize(p->stream));
-        if (nF == 0) break;
+        if (head[0] == 0 && head[5] == 0) break;  // empty frontier, nothing deferred
     }
     CK(launch_ms_finish(a, ctx->sms, p->stream));
     p->launches++;
@@ -632,6 +639,8 @@ static int ms_search_batch(hbx_pool* p, const uint32_t* ids, uint32_t nb, bool t
     if (timed) {
         p->ms_nsets += nb;
         p->ms_blocks += mc->blocks;
+        p->ms_visits += mc->visits;
+        p->ms_deferred += mc->deferred;
     }
     return HBX_OK;
 }
@@ -1478,7 +1487,7 @@ extern "C" void hbx_pool_destroy(hbx_pool* p) {
                     p->code_of_rank, p->len_of_rank, p->lut, p->dec, p->items, p->bm_sets, p->big_list,
                     p->retry_list, p->list_in, p->giant_list, p->bp_visited, p->bp_rbits, p->bp_aux, p->bp_queue, p->cnt,
                     p->alive, p->cov_huff, p->cov_bm, p->cov_raw, p->st, p->partials, p->ticket, p->d_seeds,
-                    p->d_marg, p->dec_items, p->cnt_base, p->ms_vis, p->ms_nxt, p->ms_F, p->ms_N,
+                    p->d_marg, p->dec_items, p->cnt_base, p->ms_vis, p->ms_nxt, p->ms_F, p->ms_N, p->ms_pend, p->ms_ndef,
                     p->ms_heavy, p->ms_c, p->ms_sets, p->ms_rowoff, p->ms_sparse, p->tile_live};
     for (void* b : bufs) dfree(c, b);
     if (p->ev0) cudaEventDestroy(p->ev0);
@@ -1598,6 +1607,8 @@ void fill_stats(hbx_pool* p, hbx_stats* s) {
     s->ms_kernel_s = p->ms_kernel_s;
     s->ms_sets = p->ms_nsets;
     s->ms_philox_blocks = p->ms_blocks;
+    s->ms_group_visits = p->ms_visits;
+    s->ms_deferrals = p->ms_deferred;
     s->select_kernel_s = p->select_kernel_s;
     s->select_iterations = p->select_iterations;
     s->dec_s = p->dec_s;

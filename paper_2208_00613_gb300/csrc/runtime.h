@@ -107,6 +107,7 @@ struct hbx_pool {
     uint64_t bp_words = 0;
     // bit-parallel search scratch (masks and lists of n entries each)
     uint32_t *ms_vis = nullptr, *ms_nxt = nullptr, *ms_F = nullptr, *ms_N = nullptr;  // ms_N: frontier masks
+    uint32_t *ms_pend = nullptr, *ms_ndef = nullptr;  // deferred expansions: masks, per-vertex level counts
     uint4* ms_heavy = nullptr;
     uint32_t ms_heavy_cap = 0;
     hbx::MsCounters* ms_c = nullptr;
@@ -131,7 +132,7 @@ struct hbx_pool {
     double select_kernel_s = 0, dec_s = 0, argmax_s = 0;
     uint64_t select_iterations = 0, dec_bytes = 0;
     double ms_kernel_s = 0;
-    uint64_t ms_nsets = 0, ms_blocks = 0;
+    uint64_t ms_nsets = 0, ms_blocks = 0, ms_visits = 0, ms_deferred = 0;
     bool count_pending = false;
     uint8_t* alive = nullptr;
     uint64_t alive_cap = 0;

@@ -191,6 +191,8 @@ def test_giant_ic_sets_bit_parallel(ctx, cut):
     assert st["edges_scanned"] == sc and 0 < st["edges_live"] <= lv
     assert st["rr_vertices"] == int(sizes.sum())
     assert st["sets_bitmap"] == int((cut * sizes > g.n).sum())
+    # hubs of over 512 in-edges had their expansion deferred (same sets)
+    assert st["ms_deferrals"] > 0 and st["ms_group_visits"] > 0
     if cut == 2:
         assert ((sizes > 4096) & (cut * sizes <= g.n)).sum() > 0  # some were Huffman-coded
     s, m, c = hbx.hbx_pool_select(ctx, p, T, 20)
