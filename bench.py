@@ -193,15 +193,16 @@ def sampler_roofline(stats, peak, peak_kind, wc):
 
 
 def search_roofline(stats, ceiling):
-    """Bit-parallel search of the sets that outgrow shared memory: Philox
-    blocks drawn (one per edge group and set that still needed coins) over
-    the search's CUDA-event time, against the device's measured Philox rate."""
+    """Bit-parallel search of the sets that outgrow shared memory: coin blocks
+    drawn (one Philox4x32-10 per edge group and set that still needed coins)
+    over the search's CUDA-event time, against the device's measured rate of
+    the per-pair part of those blocks (hbx_philox_ceiling)."""
     ksec = sum(s["ms_kernel_s"] for s in stats)
     blocks = sum(s["ms_philox_blocks"] for s in stats)
     if ksec <= 0 or not ceiling:
         return None
     ach = blocks / ksec / 1e9
-    return {"bound": "alu", "achieved": ach, "peak": ceiling / 1e9, "unit": "G Philox4x32-10 blocks/s",
+    return {"bound": "alu", "achieved": ach, "peak": ceiling / 1e9, "unit": "G coin blocks/s",
             "frac": ach / (ceiling / 1e9), "traffic": None, "peak_kind": "measured (hbx_philox_ceiling)",
             "kernel": "bit-parallel search (ms_light_kernel, ms_heavy_kernel, ms_compact_kernel per level)",
             "kernel_s": ksec, "blocks": blocks, "sets": int(sum(s["ms_sets"] for s in stats))}

@@ -348,12 +348,14 @@ int hbx_cancel(hbx_ticket *t);
 void hbx_ticket_destroy(hbx_ticket *t);
 
 /*
- * Measurement aid (the paper has no counterpart): the device's rate of
- * Philox4x32-10 blocks -- the arithmetic that bounds the bit-parallel search
- * of the sets that outgrow shared memory -- with every thread drawing blocks
- * back to back and touching no memory but one output word.  Best of three
- * timed launches on the context's stream after one warm-up launch.
- *   blocks_per_s  out: Philox blocks per second.
+ * Measurement aid (the paper has no counterpart): the device's rate of IC coin
+ * blocks as the bit-parallel search of the sets that outgrow shared memory
+ * computes them -- the part of Philox4x32-10 that depends on both the edge
+ * group and the set (15 of its 20 wide multiplies; the other 5 are shared by
+ * every set of a group or every group of a set) -- with every thread finishing
+ * blocks back to back and touching no memory but one output word.  Best of
+ * three timed launches on the context's stream after one warm-up launch.
+ *   blocks_per_s  out: coin blocks per second.
  * Errors: INVALID_ARG, OOM, CUDA.
  */
 int hbx_philox_ceiling(hbx_ctx *ctx, double *blocks_per_s);

@@ -22,6 +22,7 @@ struct MsCounters {
                                       // sets of the batch
     uint32_t npend;                   // vertices whose expansion the compaction being run deferred
     uint32_t force;                   // this level's compaction expands every deferred vertex
+    uint32_t lwork, hwork;            // work-stealing cursors of this level's light and heavy kernels
     unsigned long long size[MS_SETS];     // per set of the batch
     unsigned long long scanned[MS_SETS];
     unsigned long long live[MS_SETS];

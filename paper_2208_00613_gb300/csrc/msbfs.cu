@@ -46,11 +46,55 @@ constexpr uint32_t MS_CHUNK = 256;
 // L2 on the largest graphs) cost more than the Philox blocks they save.
 constexpr uint32_t MS_VIS_MIN = 4;
 
+// The IC coin block of (edge group g, set j) is Philox4x32-10 of the counter
+// (g, j, epoch, STREAM_IC).  Following its words through the first rounds:
+// round 0 multiplies g and epoch, round 1 multiplies a word that depends on j
+// alone and one that depends on g alone, and round 2 multiplies one word that
+// depends on g alone.  Those five of the twenty 32 x 32 -> 64-bit products are
+// computed once per group (three) or once per set (two), and each (group, set)
+// pair finishes with the other fifteen.  The result is the same function,
+// bit for bit.
+//
+// Group words: (w1 ^ K1[1], y2 ^ K0[2], hi(M0 x2) ^ K1[2], lo(M0 x2)), where
+// round 0 gives z1 = hi(M0 g) ^ STREAM_IC ^ K1[0], w1 = lo(M0 g), and round 1
+// gives x2 = hi(M1 z1) ^ lo(M1 epoch) ^ K0[1], y2 = lo(M1 z1).
+__device__ __forceinline__ uint4 ic_group_words(uint32_t g, uint32_t epoch, const PhiloxKeys& rk) {
+    const uint64_t p0 = (uint64_t)PHILOX_M0 * g;
+    const uint32_t z1 = (uint32_t)(p0 >> 32) ^ STREAM_IC ^ rk.k1[0], w1 = (uint32_t)p0;
+    const uint32_t le = (uint32_t)((uint64_t)PHILOX_M1 * epoch);
+    const uint64_t pz = (uint64_t)PHILOX_M1 * z1;
+    const uint32_t x2 = (uint32_t)(pz >> 32) ^ le ^ rk.k0[1], y2 = (uint32_t)pz;
+    const uint64_t px = (uint64_t)PHILOX_M0 * x2;
+    return make_uint4(w1 ^ rk.k1[1], y2 ^ rk.k0[2], (uint32_t)(px >> 32) ^ rk.k1[2], (uint32_t)px);
+}
+
+// Set words: M0 a1 (high, low) with a1 = hi(M1 epoch) ^ j ^ K0[0], the
+// round-0 output word that carries the set id.
+__device__ __forceinline__ uint2 ic_set_words(uint32_t j, uint32_t epoch, const PhiloxKeys& rk) {
+    const uint32_t a1 = (uint32_t)(((uint64_t)PHILOX_M1 * epoch) >> 32) ^ j ^ rk.k0[0];
+    const uint64_t pa = (uint64_t)PHILOX_M0 * a1;
+    return make_uint2((uint32_t)(pa >> 32), (uint32_t)pa);
+}
+
+// The pair's coin block: round 2's remaining product, then rounds 3-9.
+__device__ __forceinline__ uint4 ic_coins(uint4 G, uint2 S, const PhiloxKeys& rk) {
+    const uint64_t pm = (uint64_t)PHILOX_M1 * (S.x ^ G.x);
+    uint4 c = make_uint4((uint32_t)(pm >> 32) ^ G.y, (uint32_t)pm, G.z ^ S.y, G.w);
+#pragma unroll
+    for (int r = 3; r < 10; r++) {
+        const uint64_t p0 = (uint64_t)PHILOX_M0 * c.x, p1 = (uint64_t)PHILOX_M1 * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r],
+                       (uint32_t)p0);
+    }
+    return c;
+}
+
 // Per-warp live-edge counts of the batch's sets in shared memory, added to the
 // batch totals when the warp is done.
-__device__ __forceinline__ void ms_init_shared(const MsArgs& a, uint32_t* s_sets, uint32_t (*s_live)[MS_SETS]) {
+__device__ __forceinline__ void ms_init_shared(const MsArgs& a, uint2* s_sw, uint32_t (*s_live)[MS_SETS]) {
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < MS_SETS) s_sets[threadIdx.x] = a.sets[threadIdx.x];  // unused slots never get a bit
+    // set words of the batch's sets (unused slots never get a bit)
+    if (threadIdx.x < MS_SETS) s_sw[threadIdx.x] = ic_set_words(a.sets[threadIdx.x], a.epoch, a.rk);
     s_live[warp][lane] = 0;
     __syncthreads();
 }
@@ -67,32 +111,18 @@ __device__ __forceinline__ void ms_flush_live(const MsArgs& a, uint32_t (*s_live
 
 // One warp's staging of a round: up to MS_ROUND aligned groups of 4 in-edges,
 // two per lane (slot 2l + k holds lane l's k-th group), and for each the sets
-// that still need its coins.
+// that still need its coins.  The round's (slot, set) pairs are listed and
+// drawn MS_ITEMS at a time.
 constexpr uint32_t MS_ROUND = 64;
-constexpr uint32_t MS_ITEMS = 512;  // (slot, set) pairs listed per round; more are found by search
+constexpr uint32_t MS_ITEMS = 512;
+constexpr int MS_ILP = 2;  // pairs a lane draws at once
 struct MsRound {
-    uint16_t items[MS_ITEMS];  // slot << 5 | set of the round's first MS_ITEMS pairs
+    uint16_t items[MS_ITEMS];  // slot << 5 | set of the window's pairs
     uint4 thr[MS_ROUND];      // live thresholds of the group's edges
     uint4 um[MS_ROUND];       // per edge: sets of the frontier mask whose source is not yet visited
     uint4 em[MS_ROUND];       // per edge: sets for which it is live (filled by the items)
-    uint32_t gg[MS_ROUND];    // group index (the Philox counter's first word)
-    uint32_t need[MS_ROUND];  // union of the group's um: one Philox block per set in it
-    uint32_t scan[MS_ROUND];  // inclusive prefix sum of popc(need) over the slots
+    uint4 gw[MS_ROUND];       // group words of the coin blocks (ic_group_words)
 };
-
-// Position of the r-th (from 0) set bit of m, which has more than r set bits.
-__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
-    uint32_t pos = 0, c = __popc(m & 0xFFFFu);
-    if (r >= c) { r -= c; m >>= 16; pos += 16; }
-    c = __popc(m & 0xFFu);
-    if (r >= c) { r -= c; m >>= 8; pos += 8; }
-    c = __popc(m & 0xFu);
-    if (r >= c) { r -= c; m >>= 4; pos += 4; }
-    c = __popc(m & 0x3u);
-    if (r >= c) { r -= c; m >>= 2; pos += 2; }
-    if (r >= (m & 1u)) pos += 1;
-    return pos;
-}
 
 // One group of a round: its sources and thresholds (loaded together, so
 // both are in flight at once), then the visited masks of its sources.
@@ -137,11 +167,11 @@ __device__ __forceinline__ void ms_visited(const MsArgs& a, MsGroup& G, bool val
 // (valid[k] = false: no group).  A set needs a group's Philox block only if
 // the source of one of the vertex's edges in the group has not been visited
 // by that set: a visited source cannot join the set again, so its coin
-// decides nothing.  The (group, set) pairs that remain are spread evenly over
-// the lanes, one Philox block each; live edges into unvisited sources are
-// collected per edge in shared memory and then ORed into nxt[source] with one
-// reduction per edge.
-__device__ __forceinline__ void ms_round(const MsArgs& a, MsRound& R, const uint32_t* s_sets, uint32_t* s_live_w,
+// decides nothing.  The (group, set) pairs that remain are listed in slot
+// order, MS_ITEMS at a time, and spread evenly over the lanes, one Philox
+// block each; live edges into unvisited sources are collected per edge in
+// shared memory and then ORed into nxt[source] with one reduction per edge.
+__device__ __forceinline__ void ms_round(const MsArgs& a, MsRound& R, const uint2* s_sw, uint32_t* s_live_w,
                                          uint32_t& nblk, uint32_t& nvis, const bool* valid, const uint32_t* gg,
                                          const uint32_t* eb, const uint32_t* ee, const uint32_t* f) {
     const uint32_t lane = threadIdx.x & 31;
@@ -161,73 +191,62 @@ __device__ __forceinline__ void ms_round(const MsArgs& a, MsRound& R, const uint
     R.um[2 * lane + 1] = G1.um;
     R.em[2 * lane] = make_uint4(0, 0, 0, 0);
     R.em[2 * lane + 1] = make_uint4(0, 0, 0, 0);
-    R.gg[2 * lane] = gg[0];
-    R.gg[2 * lane + 1] = gg[1];
-    R.need[2 * lane] = G0.need;
-    R.need[2 * lane + 1] = G1.need;
-    R.scan[2 * lane] = incl - n1;
-    R.scan[2 * lane + 1] = incl;
-    {
-        // list the lane's (slot, set) pairs, in slot order
-        uint32_t o = incl - n0 - n1;
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            for (uint32_t m = k ? G1.need : G0.need; m && o < MS_ITEMS; m &= m - 1, o++)
-                R.items[o] = (uint16_t)(((2 * lane + k) << 5) | (__ffs(m) - 1));
+    if (n0) R.gw[2 * lane] = ic_group_words(gg[0], a.epoch, a.rk);
+    if (n1) R.gw[2 * lane + 1] = ic_group_words(gg[1], a.epoch, a.rk);
+    uint32_t m0 = G0.need, m1 = G1.need, o = incl - n0 - n1;  // the lane's pairs: positions [o, incl)
+    for (uint32_t w0 = 0; w0 < total; w0 += MS_ITEMS) {
+        const uint32_t wend = min(w0 + MS_ITEMS, total);
+        // list the lane's pairs that fall in this window
+        while (o < wend && o < incl) {
+            uint32_t it;
+            if (m0) {
+                it = ((2 * lane) << 5) | (uint32_t)(__ffs(m0) - 1);
+                m0 &= m0 - 1;
+            } else {
+                it = ((2 * lane + 1) << 5) | (uint32_t)(__ffs(m1) - 1);
+                m1 &= m1 - 1;
+            }
+            R.items[o - w0] = (uint16_t)it;
+            o++;
         }
-    }
-    __syncwarp();
-    // two pairs per lane per step: their Philox blocks are independent, so the
-    // rounds of one fill the other's multiply latency
-    for (uint32_t t0 = lane; t0 < total; t0 += 64) {
-        uint32_t slot[2], s[2];
-        bool have[2];
+        __syncwarp();
+        // MS_ILP pairs per lane per step: their Philox blocks are independent,
+        // so the rounds of one fill the others' multiply latency
+        for (uint32_t t0 = w0 + lane; t0 < wend; t0 += 32 * MS_ILP) {
+            uint32_t slot[MS_ILP], s[MS_ILP];
+            bool have[MS_ILP];
+            uint4 x[MS_ILP];
 #pragma unroll
-        for (int q = 0; q < 2; q++) {
-            const uint32_t t = t0 + 32 * q;
-            have[q] = t < total;
-            slot[q] = 0;
-            s[q] = 0;
-            if (!have[q]) continue;
-            if (t < MS_ITEMS) {
-                const uint32_t it = R.items[t];
+            for (int q = 0; q < MS_ILP; q++) {
+                const uint32_t t = t0 + 32 * q;
+                have[q] = t < wend;
+                const uint32_t it = have[q] ? (uint32_t)R.items[t - w0] : 0u;
                 slot[q] = it >> 5;
                 s[q] = it & 31u;
-            } else {
-                // past the list: slot = number of slots whose inclusive count is <= t
-                uint32_t sl = 0;
+            }
 #pragma unroll
-                for (uint32_t step = MS_ROUND / 2; step; step >>= 1)
-                    if (R.scan[sl + step - 1] <= t) sl += step;
-                const uint32_t nd = R.need[sl];
-                slot[q] = sl;
-                s[q] = nth_set_bit(nd, t - (R.scan[sl] - (uint32_t)__popc(nd)));
+            for (int q = 0; q < MS_ILP; q++) x[q] = ic_coins(R.gw[slot[q]], s_sw[s[q]], a.rk);
+#pragma unroll
+            for (int q = 0; q < MS_ILP; q++) {
+                if (!have[q]) continue;
+                const uint4 th = R.thr[slot[q]], u = R.um[slot[q]];
+                const uint32_t bit = 1u << s[q];
+                const bool l0 = (u.x & bit) && ic_live(x[q].x, th.x);
+                const bool l1 = (u.y & bit) && ic_live(x[q].y, th.y);
+                const bool l2 = (u.z & bit) && ic_live(x[q].z, th.z);
+                const bool l3 = (u.w & bit) && ic_live(x[q].w, th.w);
+                if (l0 | l1 | l2 | l3) {
+                    uint32_t* em = reinterpret_cast<uint32_t*>(&R.em[slot[q]]);
+                    if (l0) atomicOr(em + 0, bit);
+                    if (l1) atomicOr(em + 1, bit);
+                    if (l2) atomicOr(em + 2, bit);
+                    if (l3) atomicOr(em + 3, bit);
+                    atomicAdd(&s_live_w[s[q]], (uint32_t)l0 + (uint32_t)l1 + (uint32_t)l2 + (uint32_t)l3);
+                }
             }
         }
-        uint4 x[2];
-#pragma unroll
-        for (int q = 0; q < 2; q++)
-            x[q] = philox4x32_10_rk(make_uint4(R.gg[slot[q]], s_sets[s[q]], a.epoch, STREAM_IC), a.rk);
-#pragma unroll
-        for (int q = 0; q < 2; q++) {
-            if (!have[q]) continue;
-            const uint4 th = R.thr[slot[q]], u = R.um[slot[q]];
-            const uint32_t bit = 1u << s[q];
-            const bool l0 = (u.x & bit) && ic_live(x[q].x, th.x);
-            const bool l1 = (u.y & bit) && ic_live(x[q].y, th.y);
-            const bool l2 = (u.z & bit) && ic_live(x[q].z, th.z);
-            const bool l3 = (u.w & bit) && ic_live(x[q].w, th.w);
-            if (l0 | l1 | l2 | l3) {
-                uint32_t* em = reinterpret_cast<uint32_t*>(&R.em[slot[q]]);
-                if (l0) atomicOr(em + 0, bit);
-                if (l1) atomicOr(em + 1, bit);
-                if (l2) atomicOr(em + 2, bit);
-                if (l3) atomicOr(em + 3, bit);
-                atomicAdd(&s_live_w[s[q]], (uint32_t)l0 + (uint32_t)l1 + (uint32_t)l2 + (uint32_t)l3);
-            }
-        }
+        __syncwarp();  // the window's list is rewritten by the next one
     }
-    __syncwarp();
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const uint4 em = R.em[2 * lane + k];
@@ -250,18 +269,23 @@ __global__ void ms_start_kernel(MsArgs a) {
 }
 
 __global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
-    __shared__ uint32_t s_sets[MS_SETS];
+    __shared__ uint2 s_sw[MS_SETS];
     __shared__ uint32_t s_live[MS_WARPS][MS_SETS];
     __shared__ uint32_t w_scan[MS_WARPS][32], w_g0[MS_WARPS][32], w_eb[MS_WARPS][32], w_ee[MS_WARPS][32],
         w_f[MS_WARPS][32];
     __shared__ MsRound s_round[MS_WARPS];
     const uint32_t nF = a.mc->nF;
     if (blockIdx.x * MS_WARPS * 32 >= nF) return;  // thin level: this block has no chunk
-    ms_init_shared(a, s_sets, s_live);
+    ms_init_shared(a, s_sw, s_live);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * MS_WARPS * 32;
     uint32_t nblk = 0, nvis = 0;
-    for (uint32_t c = (blockIdx.x * MS_WARPS + warp) * 32; c < nF; c += stride) {
+    for (;;) {
+        // the next 32 frontier vertices (work stealing: the cost of a chunk
+        // varies with its vertices' degrees and masks)
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&a.mc->lwork, 32u);
+        c = __shfl_sync(0xFFFFFFFFu, c, 0);
+        if (c >= nF) break;
         const uint32_t i = c + lane;
         uint32_t v = 0, f = 0, b = 0, e = 0, gfirst = 0, ng = 0;
         if (i < nF) {
@@ -313,7 +337,7 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
                     ff[k] = w_f[warp][lo];
                 }
             }
-            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, nvis, ok, gg, eb, ee, ff);
+            ms_round(a, s_round[warp], s_sw, s_live[warp], nblk, nvis, ok, gg, eb, ee, ff);
         }
         __syncwarp();
     }
@@ -321,22 +345,26 @@ __global__ void __launch_bounds__(MS_THREADS, 4) ms_light_kernel(MsArgs a) {
 }
 
 __global__ void __launch_bounds__(MS_THREADS, 4) ms_heavy_kernel(MsArgs a) {
-    __shared__ uint32_t s_sets[MS_SETS];
+    __shared__ uint2 s_sw[MS_SETS];
     __shared__ uint32_t s_live[MS_WARPS][MS_SETS];
     __shared__ MsRound s_round[MS_WARPS];
     const uint32_t nH = min(a.mc->nH, a.heavy_cap);
     if (blockIdx.x * MS_WARPS >= nH) return;
-    ms_init_shared(a, s_sets, s_live);
+    ms_init_shared(a, s_sw, s_live);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t nblk = 0, nvis = 0;
-    for (uint32_t it = blockIdx.x * MS_WARPS + warp; it < nH; it += gridDim.x * MS_WARPS) {
-        const uint4 item = a.heavy[it];  // one chunk per warp
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(&a.mc->hwork, 1u);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it >= nH) break;
+        const uint4 item = a.heavy[it];  // one chunk per warp (work stealing)
         const uint32_t eb = __ldg(a.g.row_ptr + item.x), ee = __ldg(a.g.row_ptr + item.x + 1);
         for (uint32_t g = item.y; g < item.z; g += MS_ROUND) {
             const bool ok[2] = {g + lane < item.z, g + 32 + lane < item.z};
             const uint32_t gg[2] = {g + lane, g + 32 + lane}, ebs[2] = {eb, eb}, ees[2] = {ee, ee};
             const uint32_t ff[2] = {item.w, item.w};
-            ms_round(a, s_round[warp], s_sets, s_live[warp], nblk, nvis, ok, gg, ebs, ees, ff);
+            ms_round(a, s_round[warp], s_sw, s_live[warp], nblk, nvis, ok, gg, ebs, ees, ff);
         }
     }
     ms_flush_live(a, s_live, nblk, nvis);
@@ -438,6 +466,8 @@ __global__ void ms_advance_kernel(MsArgs a) {
     c->nN = 0;
     c->nH = 0;
     c->npend = 0;
+    c->lwork = 0;
+    c->hwork = 0;
 }
 
 // Size and scanned in-edges of each set of the batch, from the visited masks:
@@ -643,18 +673,20 @@ cudaError_t launch_ms_emit(const MsArgs& a, uint32_t dense, uint32_t mode, uint6
 }  // namespace hbx
 
 // ---------------------------------------------------------------------------
-// Philox throughput ceiling: every thread draws `per_thread` blocks back to
-// back (distinct counters, the search's key) and folds them into one word, so
-// the kernel does nothing but the bit-parallel search's arithmetic.  Its rate
-// is the ALU roofline of that search.
+// Coin-block throughput ceiling: every thread finishes `per_thread` coin
+// blocks back to back (the per-pair remainder of Philox4x32-10 that the search
+// computes for each (edge group, set) pair, from distinct group words) and
+// folds them into one word, so the kernel does nothing but the search's
+// per-pair arithmetic.  Its rate is the ALU roofline of that search.
 // ---------------------------------------------------------------------------
 namespace hbx {
 
 __global__ void __launch_bounds__(256) philox_ceiling_kernel(uint32_t per_thread, PhiloxKeys rk, uint32_t* out) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint2 S = ic_set_words(tid, 0u, rk);
     uint32_t acc = 0;
     for (uint32_t i = 0; i < per_thread; i++) {
-        const uint4 x = philox4x32_10_rk(make_uint4(i, tid, 0u, STREAM_IC), rk);
+        const uint4 x = ic_coins(make_uint4(i, tid ^ i, i * 0x9E3779B9u, tid + i), S, rk);
         acc ^= x.x ^ x.y ^ x.z ^ x.w;
     }
     out[tid] = acc;
