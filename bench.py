@@ -155,8 +155,9 @@ def oracle_sample_size(g, w, target_s, cores):
 def oracle_baseline(g, w, target_s=15.0):
     cores = os.cpu_count() or 1
     if w.name == "ic_rmat42m":
-        # a fifth of this graph's sets reach most of it (about 70 s each on one
-        # core): one set per core, all cores at once
+        # a fifth of this graph's sets reach most of it (40-70 s each on one
+        # core), the others are a single vertex: one set per core, all cores at
+        # once (sets [0, cores) hold giant ones in about that share)
         S = cores
     else:
         S = oracle_sample_size(g, w, target_s, cores)
@@ -390,17 +391,19 @@ def run_reference(args, rank):
     model = oracle.IC if w.model == "IC" else oracle.LT
     times = []
     if w.name == "ic_rmat42m":
-        # one RR set per step on one thread (set id = step index): a fifth of
-        # this graph's sets take about a minute each, so a step of one set per
-        # core would take a minute almost every time
+        # one RR set per step on one thread.  This graph's sets are either a
+        # single vertex or reach 7.8 M vertices (about a fifth of them, 40-60 s
+        # each on one core), and runs of consecutive ids can miss the giant ones,
+        # so the ids are spread by a prime stride: 1000 + 7919 i for step i
         cores = 1
-        for i in range(args.warmup + args.steps):
+        ids = [1000 + 7919 * i for i in range(args.warmup + args.steps)]
+        for i, j in enumerate(ids):
             t0 = time.perf_counter()
-            oracle.rr_set(g, model, w.rr_seed, 0, i)
+            oracle.rr_set(g, model, w.rr_seed, 0, j)
             if i >= args.warmup:
                 times.append(time.perf_counter() - t0)
         S = 1
-        sample = (f"one RR set of {w.name} per step (set id = step index, ids {args.warmup}..{args.warmup + args.steps - 1} "
+        sample = (f"one RR set of {w.name} per step, set ids 1000 + 7919 i (i = {args.warmup}..{args.warmup + args.steps - 1} "
                   f"timed), one thread")
     else:
         cores = os.cpu_count() or 1
