@@ -528,19 +528,19 @@ def run_hbx(args, rank, world, local_rank):
                                                             imm_ms, r))
         else:
             skipped["plain_form"] = "time budget"
+    serving = None
+    if args.serving:
+        if left() > 60:  # 200 queries at 20/s on three small graphs: about 30 s
+            serving = guarded("serving", lambda: serving_leg(hbx, synth, tc, args.serving))
+        else:
+            skipped["serving"] = "time budget"
     secondary = None
     if args.secondary and world == 1:
-        if left() > 90:
+        if left() > 40:  # 15 IMMs of ~25 ms plus its oracle sample: about 20 s
             secondary = guarded("secondary", lambda: secondary_leg(hbx, synth, tc, args.secondary, 12, 3, flush, peak,
                                                                    peak_kind, not args.no_cpu_baseline))
         else:
             skipped["secondary"] = "time budget"
-    serving = None
-    if args.serving:
-        if left() > 180:
-            serving = guarded("serving", lambda: serving_leg(hbx, synth, tc, args.serving))
-        else:
-            skipped["serving"] = "time budget"
 
     s0 = stats[-1]
     search = search_roofline(stats, ceiling)
