@@ -596,7 +596,7 @@ def ctypes_sizeof_stats(hbx):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hbx", choices=["hbx", "reference"])
     ap.add_argument("--workload", default="ic_rmat42m")
