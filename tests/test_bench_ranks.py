@@ -100,3 +100,56 @@ def test_count_roofline_from_stats():
     r = bench.count_roofline(stats, 6000.0)
     assert abs(r["achieved"] - 3000.0) < 1e-9 and abs(r["frac"] - 0.5) < 1e-12
     assert bench.count_roofline([{"count_kernel_s": 0.0, "count_bytes": 0}], 6000.0) is None
+
+
+def test_serving_leg_counts_admission_refusals():
+    """A query that admission control refuses at submission (its projected pool
+    does not fit the device) is counted as refused; the leg still reports the
+    other queries instead of ending the bench run."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Err(RuntimeError):
+        pass
+
+    graphs = {}
+
+    class FakeHbx:
+        HbxError = Err
+
+        @staticmethod
+        def hbx_graph_create(ctx, g):
+            graphs[len(graphs)] = g
+            return len(graphs) - 1
+
+        hbx_graph_destroy = staticmethod(lambda h: None)
+        hbx_server_create = staticmethod(lambda ctx, inflight, budget: "srv")
+        hbx_server_destroy = staticmethod(lambda srv: None)
+        hbx_ticket_destroy = staticmethod(lambda t: None)
+
+        @staticmethod
+        def hbx_submit(ctx, srv, graph, model, k, eps, ell, seed):
+            if eps == 0.13 and graph == 2:
+                raise Err("ADMISSION: projected footprint exceeds the budget")
+            return (graph, k)
+
+        @staticmethod
+        def hbx_wait(t, k):
+            return 0, {"latency_s": 0.001 * (1 + t[1] % 7)}
+
+    class G:
+        lt_weight = None
+        prob = None
+
+    fake_synth = types.SimpleNamespace(
+        WORKLOADS={n: types.SimpleNamespace(graph=lambda: G(), graph_seed=1)
+                   for n in ("ic_rmat4k", "wc_rmat1m", "lt_rmat4m")},
+        lt_weights=lambda g, s: "w", ic_uniform=lambda g, s, p: "p",
+        poisson_queries=lambda seed, count, rate_per_s, graphs: [
+            dict(t=0.0, graph=i % 3, model="IC", k=10 + i, eps=(0.13, 0.5)[i % 2]) for i in range(count)])
+    out = bench.serving_leg(FakeHbx, fake_synth, types.SimpleNamespace(ctx=None), 12, rate=1e6)
+    refused = sum(1 for i in range(12) if i % 3 == 2 and i % 2 == 0)
+    assert out["rejected"] == refused and out["completed"] == 12 - refused and out["failed"] == 0
+    assert all(r["eps"] == 0.13 and r["graph"] == 2 for r in out["rejected_queries"])
+    assert out["p50_ms"] > 0 and out["queries_per_s"] > 0
