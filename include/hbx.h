@@ -109,8 +109,11 @@ typedef struct {
      * covered sets' vertices each iteration.  1: rebuild the counts from the
      * sets not yet covered every iteration, as Algorithms 2 and 3 print it
      * (Bitmax tiles: POPCOUNT of each row under the live-set mask, i.e. after
-     * Eq. (3)'s SUBTRACT).  The seeds are the same either way; the plain form
-     * always decrements. */
+     * Eq. (3)'s SUBTRACT).  2: choose per iteration, as Ripples' update-or-
+     * recount counting does (Section 2.2): recount when the chosen vertex
+     * covers more than half of the sets still live (the rest are then fewer
+     * to read than the covered ones), decrement otherwise.  The seeds are the
+     * same in every mode; the plain form always decrements. */
     uint32_t select_mode;
     /* IMM's final phase: 0 reuses the estimation rounds' sets (theta =
      * max(T_i, ceil(lambda* / LB)) sets [0, theta)); 1 draws theta =

@@ -128,7 +128,8 @@ struct SelArgs {
     unsigned long long* marginal;          // [k]
     int sms;
     long long wait_cycles;                 // bound of every grid-barrier wait
-    uint32_t select_mode;                  // 0: decrement; 1: recount every iteration (persistent form)
+    uint32_t select_mode;                  // 0: decrement; 1: recount every iteration; 2: recount when
+                                           // u* covers over half of the live sets (persistent form)
     // Bitmax pools in vertex-major tiles: every set is a column of a tile
     // (tile t at word t * n4w of bm_heap, word v bit s = set 32t + s)
     uint32_t tiles;

@@ -1446,8 +1446,8 @@ extern "C" int hbx_pool_create(hbx_ctx* ctx, hbx_graph* g, hbx_model model, uint
         return fail(ctx, HBX_ERR_INVALID_ARG, "warp_capacity must be a power of two in [64, 2048]");
     if (o.block_cluster > 8 || (o.block_cluster & (o.block_cluster - 1)))
         return fail(ctx, HBX_ERR_INVALID_ARG, "block_cluster must be 0, 1, 2, 4 or 8");
-    if (o.scheme > 1 || o.select_mode > 1 || o.fresh_final > 1)
-        return fail(ctx, HBX_ERR_INVALID_ARG, "scheme, select_mode and fresh_final are 0 or 1");
+    if (o.scheme > 1 || o.select_mode > 2 || o.fresh_final > 1)
+        return fail(ctx, HBX_ERR_INVALID_ARG, "scheme and fresh_final are 0 or 1, select_mode 0, 1 or 2");
     if (o.scheme && !o.encode) return fail(ctx, HBX_ERR_INVALID_ARG, "the per-graph scheme needs encode = 1");
     if (g->n >= 0xFFFFFFFFu && o.scheme) return fail(ctx, HBX_ERR_INVALID_ARG, "graph too large for the Bitmax cut");
     cudaSetDevice(ctx->device);

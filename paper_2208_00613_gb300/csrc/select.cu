@@ -635,6 +635,7 @@ __global__ void __launch_bounds__(PS_THREADS) select_persistent_kernel(SelArgs a
     __shared__ unsigned long long s_off[BM_BATCH];
     __shared__ unsigned long long s_w[PS_THREADS / 32];
     __shared__ uint32_t s_n, s_u;
+    __shared__ int s_cu;  // count of u* (the live sets it covers)
     __shared__ bool s_ok;
     const uint32_t nb = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t hot = min(a.hot, PS_HOT);
@@ -689,6 +690,7 @@ __global__ void __launch_bounds__(PS_THREADS) select_persistent_kernel(SelArgs a
                 unsigned long long r = 0;
                 for (int w = 0; w < PS_THREADS / 32; w++) r = s_w[w] > r ? s_w[w] : r;
                 s_u = 0xFFFFFFFFu - (uint32_t)r;
+                s_cu = (int)(uint32_t)(r >> 32) - 1;
                 if (blockIdx.x == 0) {
                     a.seeds[it] = s_u;
                     a.st->u = s_u;
@@ -697,6 +699,13 @@ __global__ void __launch_bounds__(PS_THREADS) select_persistent_kernel(SelArgs a
             __syncthreads();
         }
         const uint32_t u = s_u;
+        // recount or decrement this iteration: mode 1 always recounts; mode 2
+        // (adaptive) recounts when u* covers more than half of the live sets,
+        // so that counting the rest from scratch reads less than decrementing
+        // the covered ones.  Every block decides alike (same counters, read
+        // after the barrier); both forms leave the same counts.
+        const unsigned long long live = (unsigned long long)(a.T - a.j_lo) - __ldcg(&a.st->covered);
+        const bool recount = a.select_mode == 1 || (a.select_mode == 2 && s_cu > 0 && 2ull * (unsigned)s_cu > live);
         if (timer) {
             const unsigned long long t = globaltimer_ns();
             t_a += t - t_prev;
@@ -732,9 +741,9 @@ __global__ void __launch_bounds__(PS_THREADS) select_persistent_kernel(SelArgs a
                         if (slot < a.dec_cap) a.dec_items[slot] = ((unsigned long long)t << 32) | m;
                         else atomicMax(&a.st->pad, 2u);
                     }
-                    if (a.select_mode) a.tile_live[t] = am & ~m;
+                    if (recount) a.tile_live[t] = am & ~m;
                 }
-            } else if (a.select_mode) {
+            } else if (recount) {
                 const uint32_t ru = a.has_cb ? __ldg(a.cb.rank_of + u) : NONE;
                 for (uint32_t jb = (blockIdx.x * PS_THREADS + (threadIdx.x & ~31u)); jb < a.T; jb += nb * PS_THREADS)
                     gain += cover_warp(a, u, ru, jb);
@@ -782,7 +791,7 @@ __global__ void __launch_bounds__(PS_THREADS) select_persistent_kernel(SelArgs a
                 const int c = __ldcg(a.cnt + v);
                 if (c < 0) continue;
                 uint32_t acc = 0;
-                if (a.select_mode) {
+                if (recount) {
                     for (uint32_t t = 0; t < ntiles; t++)
                         acc += __popc(__ldg(a.bm_heap + (uint64_t)t * a.n4w + v) & __ldcg(a.tile_live + t));
                     a.cnt[v] = (int)acc;
@@ -795,8 +804,8 @@ __global__ void __launch_bounds__(PS_THREADS) select_persistent_kernel(SelArgs a
                 }
             }
             if (timer)
-                atomicAdd(&a.st->dec_bytes, 4ull * (a.select_mode ? (unsigned long long)ntiles : n_cov) * a.n4w);
-        } else if (a.select_mode) {
+                atomicAdd(&a.st->dec_bytes, 4ull * (recount ? (unsigned long long)ntiles : n_cov) * a.n4w);
+        } else if (recount) {
             for (uint32_t i = threadIdx.x; i < hot; i += PS_THREADS) hist[i] = 0;
             __syncthreads();
             // every chunk of the sets still live

@@ -5,10 +5,11 @@
   Bitmax stores every set as a column of the vertex-major 32-set tiles of
   Section 4.2.3 / Eq. (3).  Sets, encodings, seeds and IMM results equal the
   oracle's.
-- Recount-from-scratch selection (Algorithms 2 and 3 as printed) on Huffman,
-  bitmap-row, tile and uncompressed pools: seeds, marginal gains and coverage
-  equal the oracle's greedy, its per-iteration recount and, for tiles, its
-  BitmaxQuery (POPCOUNT / SUBTRACT).
+- Recount-from-scratch selection (Algorithms 2 and 3 as printed) and the
+  adaptive choice between recounting and decrementing on Huffman, bitmap-row,
+  tile and uncompressed pools: seeds, marginal gains and coverage equal the
+  oracle's greedy, its per-iteration recount and, for tiles, its BitmaxQuery
+  (POPCOUNT / SUBTRACT).
 """
 import numpy as np
 import pytest
@@ -92,15 +93,16 @@ def test_scheme_bitmax_tiles(ctx):
             assert s.tolist() == so.tolist() and m.tolist() == mo.tolist() and c == co
     finally:
         hbx.hbx_pool_destroy(p)
-    p = hbx.hbx_pool_create(ctx, G, "IC", 13, hbx.hbx_default_options(encode=1, warmup_sets=W, scheme=1,
-                                                                      select_mode=1))
-    try:
-        hbx.hbx_pool_extend(ctx, p, T)
-        s, m, c = hbx.hbx_pool_select(ctx, p, T, 20)
-        so, mo, co = op.greedy_recount(T, 20)
-        assert s.tolist() == so.tolist() and m.tolist() == mo.tolist() and c == co
-    finally:
-        hbx.hbx_pool_destroy(p)
+    for mode in (1, 2):  # recount, adaptive (the first seeds cover most sets here)
+        p = hbx.hbx_pool_create(ctx, G, "IC", 13, hbx.hbx_default_options(encode=1, warmup_sets=W, scheme=1,
+                                                                          select_mode=mode))
+        try:
+            hbx.hbx_pool_extend(ctx, p, T)
+            s, m, c = hbx.hbx_pool_select(ctx, p, T, 20)
+            so, mo, co = op.greedy_recount(T, 20)
+            assert s.tolist() == so.tolist() and m.tolist() == mo.tolist() and c == co, mode
+        finally:
+            hbx.hbx_pool_destroy(p)
     # the whole IMM under the per-graph scheme, against the oracle's IMM
     r = hbx.hbx_imm(ctx, G, "IC", 10, 0.5, 1.0, 13, hbx.hbx_default_options(scheme=1))
     ro = oracle.Pool(g, oracle.IC, 13).imm(10, 0.5, 1.0)
@@ -161,7 +163,7 @@ def test_recount_selection(ctx, kind):
     ref = op.greedy(T, k)
     assert [x.tolist() if hasattr(x, "tolist") else x for x in op.greedy_recount(T, k)] == \
         [x.tolist() if hasattr(x, "tolist") else x for x in ref]
-    for mode in (0, 1):
+    for mode in (0, 1, 2):  # decrement, recount, adaptive
         p = hbx.hbx_pool_create(ctx, G, "IC", 21, hbx.hbx_default_options(select_mode=mode, **o))
         try:
             hbx.hbx_pool_extend(ctx, p, T)
